@@ -1,0 +1,231 @@
+"""Pins of the oracle's time stepping, initialisation and boundary schemes against closed forms,
+invariants and the convergence orders the paper reports (arXiv:2410.13165, Secs. 2-5)."""
+import os
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _paper_crs():
+    out = {}
+    with open(os.path.join(GOLDEN, "paper_convergence_rates.txt")) as fh:
+        for line in fh:
+            if line.strip() and not line.startswith("#"):
+                t, case, *rest = line.split()
+                out[(t, case, tuple(float(v) for v in rest[:-1]))] = float(rest[-1])
+    return out
+
+
+def _fourier_wave(m, rng, nmodes=4, L=1.0):
+    a = rng.uniform(-1, 1, nmodes)
+    kap = [2 * np.pi * rng.integers(1, 4, m.d) / L for _ in range(nmodes)]
+    th = rng.uniform(0, 2 * np.pi, nmodes)
+    return m.wave(a=a, kappa=kap, theta=th)
+
+
+# ----------------------------------------------------------------- von Neumann analysis (Sec. 4.2)
+
+def _G_paper(d, sigma, xi, s=2.0):
+    """Eq. (G): G = M T M^{-1} ((1-s) I + s eps e_1^T) with T = diag(exp(-i c_k . xi)) (the i restored),
+    for s = 2 the paper's (2 eps (x) e_1 - I)."""
+    M = O.moment_matrix(d)
+    e = O.velocities(d)
+    eps = O.eps(d, sigma, O.m4_rule(d, sigma))
+    Q = M.shape[0]
+    T = np.diag(np.exp(-1j * (e @ xi)))
+    E1 = np.zeros(Q)
+    E1[0] = 1.0
+    C = (1 - s) * np.eye(Q) + s * np.outer(eps, E1)
+    return M @ T @ np.linalg.inv(M) @ C
+
+
+@pytest.mark.parametrize("d,sigma,tau", [(2, (0.1, 0.2), 0.5), (2, (0.4, -0.3), 0.5), (3, (0.1, -0.05, 0.2), 0.5),
+                                         (2, (0.1, 0.2), 0.8), (1, (0.3,), 0.5)])
+def test_one_step_on_a_fourier_mode_is_the_amplification_matrix(d, sigma, tau):
+    N = 6
+    m = O.Model(d, N, 0.0, 1.0, sigma, tau=tau)
+    rng = np.random.default_rng(1)
+    X = np.round(m.coords() / m.dx).astype(int)                  # integer lattice coordinates
+    for _ in range(3):
+        mvec = rng.integers(0, N, d)
+        xi = 2 * np.pi * mvec / N
+        a = rng.normal(size=m.Q) + 1j * rng.normal(size=m.Q)
+        phase = np.exp(1j * (xi @ X))                             # (S,)
+        f = a[:, None] * phase[None, :]
+        fr = m.step(np.ascontiguousarray(f.real))
+        fi = m.step(np.ascontiguousarray(f.imag))
+        got = fr + 1j * fi
+        Gm = _G_paper(d, np.asarray(sigma), xi, 1.0 / tau)      # moment space
+        Mm = O.moment_matrix(d)
+        want_a = np.linalg.solve(Mm, Gm @ (Mm @ a))              # population space
+        assert np.max(np.abs(got - want_a[:, None] * phase[None, :])) < 1e-13
+
+
+def test_spectral_radius_inside_and_outside_the_region():
+    rho_in, rho_out = 0.0, 0.0
+    for k1 in range(16):
+        for k2 in range(16):
+            xi = 2 * np.pi * np.array([k1, k2]) / 16
+            rho_in = max(rho_in, np.max(np.abs(np.linalg.eigvals(_G_paper(2, np.array([0.1, 0.2]), xi)))))
+            rho_out = max(rho_out, np.max(np.abs(np.linalg.eigvals(_G_paper(2, np.array([0.6, 0.1]), xi)))))
+    assert rho_in < 1 + 1e-12
+    assert rho_out > 1.05
+
+
+def test_uniform_state_returns_after_two_steps():
+    """xi = 0: G = 2 eps (x) e_1 - I satisfies G^2 = I (Eq. (G-3)); any spatially uniform
+    population vector (not only equilibria) recurs after two steps when R = 0, s = 2."""
+    m = O.Model(3, 4, 0.0, 1.0, (0.1, 0.05, -0.2))
+    rng = np.random.default_rng(3)
+    f = np.repeat(rng.normal(size=(m.Q, 1)), m.S, axis=1)
+    f2 = m.step(f, nsteps=2)
+    assert np.max(np.abs(f2 - f)) < 1e-14
+
+
+def test_d1q3_eigenvalues_at_sigma_minus_half():
+    """Appendix D: for sigma = -1/2 the amplification matrix has eigenvalues -e^{i xi}, +-e^{-i xi/2}
+    (up to the sign convention of the Fourier variable; the push scheme gives the conjugates)."""
+    N = 8
+    m = O.Model(1, N, 0.0, 1.0, (-0.5,))
+    X = np.arange(N)
+    for kk in range(1, N):
+        xi = 2 * np.pi * kk / N
+        phase = np.exp(1j * xi * X)
+        G = np.zeros((3, 3), complex)
+        for j in range(3):
+            f = np.zeros((3, N), complex)
+            f[j] = phase
+            got = m.step(np.ascontiguousarray(f.real)) + 1j * m.step(np.ascontiguousarray(f.imag))
+            G[:, j] = got[:, 0] / phase[0]
+        ev = np.sort_complex(np.linalg.eigvals(G))
+        paper = np.array([-np.exp(1j * xi), np.exp(-1j * xi / 2), -np.exp(-1j * xi / 2)])
+        want = np.sort_complex(np.conj(paper))
+        assert np.max(np.abs(ev - want)) < 1e-12
+
+
+# ----------------------------------------------------------------- invariants
+
+@pytest.mark.parametrize("bc", ["periodic", "fullway", "halfway"])
+def test_uniform_field_grows_exactly_by_the_source(bc):
+    m = O.Model(2, 9, 0.0, 1.0, (0.1, -0.2), R=5.0, bc=bc)
+    w = m.wave(b=0.7)
+    f = m.init(np.full(m.S, 0.7), np.zeros((2, m.S)), order=3)
+    n = 13
+    f = m.step(f, 0, n, wave=w)
+    assert np.max(np.abs(m.phi(f) - (0.7 + n * m.dt * 5.0))) < 1e-13
+
+
+def test_mass_is_conserved_up_to_the_source():
+    m = O.Model(2, 16, 0.0, 1.0, (0.1, 0.2), R=3.0, tau=0.8)
+    rng = np.random.default_rng(5)
+    f = m.init(rng.normal(size=m.S), order=3)
+    mass0 = m.phi(f).sum()
+    n = 20
+    f = m.step(f, 0, n)
+    assert abs(m.phi(f).sum() - (mass0 + n * m.S * m.dt * 3.0)) < 1e-10
+
+
+def test_entropy_is_conserved_for_s2_and_not_otherwise():
+    """Remark 6: with s = 2, periodic boundaries and R = 0 the total kinetic entropy (Eq. (skfk)) is
+    conserved; it decays for s != 2."""
+    rng = np.random.default_rng(6)
+    m = O.Model(2, 16, 0.0, 1.0, (0.1, 0.2))
+    f = m.init(rng.normal(size=m.S), order=3)
+    H0 = m.entropy(f)
+    H = m.entropy(m.step(f, 0, 64))
+    assert abs(H - H0) < 1e-13 * H0
+    m8 = O.Model(2, 16, 0.0, 1.0, (0.1, 0.2), tau=0.8)
+    f8 = m8.init(rng.normal(size=m8.S), order=3)
+    assert m8.entropy(m8.step(f8, 0, 64)) < 0.99 * m8.entropy(f8)
+
+
+@pytest.mark.parametrize("bc", ["fullway", "halfway"])
+@pytest.mark.parametrize("u", [(0.1, 0.2), (0.4, 0.4)])
+def test_linear_field_is_reproduced_exactly(bc, u):
+    """phi = b + g.(x - u t) + R t: third-order init and order-4 boundaries are exact for it."""
+    m = O.Model(2, 11, 0.0, 1.0, u, R=2.0, bc=bc)
+    w = m.wave(b=0.3, g=(1.5, -0.7))
+    f = m.init(m.exact(w, 0.0), m.exact_grad(w, 0.0), order=3)
+    n = 12
+    f = m.step(f, 0, n, wave=w)
+    assert np.max(np.abs(m.phi(f) - m.exact(w, n * m.dt))) < 1e-12
+
+
+# ----------------------------------------------------------------- convergence orders
+
+def _periodic_error(N, order, u=(0.1, 0.2), T=0.5):
+    m = O.Model(2, N, 0.0, 1.0, u)
+    rng = np.random.default_rng(11)
+    w = _fourier_wave(m, rng)
+    f = m.init(m.exact(w, 0.0), m.exact_grad(w, 0.0), order=order)
+    n = int(round(T / m.dt))
+    f = m.step(f, 0, n)
+    return O.rmse(m.phi(f), m.exact(w, n * m.dt))
+
+
+def _slopes(errs):
+    return [np.log2(a / b) for a, b in zip(errs, errs[1:])]
+
+
+def test_periodic_convergence_fourth_order_with_third_order_init():
+    """Table 2 pattern: CR ~ 4 with the third-order initialisation."""
+    sl = _slopes([_periodic_error(N, 3) for N in (16, 32, 64)])
+    cr = _paper_crs()[("table2", "K3", (0.1, 0.2))]
+    assert all(3.6 < s < 4.6 for s in sl), sl
+    assert abs(sl[-1] - 4.0) < abs(cr - 4.0) + 0.3
+
+
+def test_periodic_convergence_second_order_with_first_order_init():
+    """Table 2 pattern: CR ~ 2 with f = f^eq initially."""
+    sl = _slopes([_periodic_error(N, 1) for N in (16, 32, 64)])
+    assert all(1.7 < s < 2.5 for s in sl), sl
+
+
+def _dirichlet_error(bc, order, K, N, u, T=1.0, R=5.0):
+    m = O.Model(2, N, 0.0, 1.0, u, R=R, bc=bc, bc_order=order)
+    w = m.wave(a=[1.0, 0.5], kappa=[(np.pi, np.pi), (2.0, -1.0)], theta=[0.3, 1.1], b=0.2)
+    f = m.init(m.exact(w, 0.0), m.exact_grad(w, 0.0), order=K)
+    n = int(round(T / m.dt))
+    f = m.step(f, 0, n, wave=w)
+    return O.rmse(m.phi(f), m.exact(w, n * m.dt))
+
+
+def test_fullway_order4_convergence():
+    """Table 1 (full-way, order-4 boundary, K = 3): CR ~ 3.8-3.9."""
+    errs = [_dirichlet_error("fullway", 4, 3, N + 1, (0.1, 0.1)) for N in (10, 20, 40)]
+    sl = _slopes(errs)
+    assert all(3.4 < s < 4.5 for s in sl), sl
+
+
+def test_halfway_order4_convergence_at_small_velocity():
+    """Table 1 (half-way, order 4, u = (0.01, 0.01)): CR ~ 3.8."""
+    errs = [_dirichlet_error("halfway", 4, 3, N, (0.01, 0.01)) for N in (10, 20, 40)]
+    sl = _slopes(errs)
+    assert all(3.4 < s < 4.6 for s in sl), sl
+
+
+@pytest.mark.parametrize("P,K,Z", [(1, 3, 1), (3, 3, 3), (4, 1, 2)])
+def test_order_law_fullway(P, K, Z):
+    """Eq. (cr-estimation): Z = min(K + 1, P) for the full-way scheme."""
+    errs = [_dirichlet_error("fullway", P, K, N + 1, (0.1, 0.1)) for N in (20, 40, 80)]
+    sl = _slopes(errs)
+    assert abs(sl[-1] - Z) < 0.45, sl
+
+
+def test_halfway_diverges_where_fullway_converges():
+    """Table 1 pattern at T = 10: with u = (0.1, 0.1) (entropy- and L2-stable bulk) the half-way
+    scheme's error grows under refinement while the full-way scheme converges at ~4th order; at
+    u = (0.01, 0.01) both converge, and full-way converges even at u = (0.4, 0.4)."""
+    def errs(bc, u, offset):
+        return [_dirichlet_error(bc, 4, 3, N + offset, u, T=10.0) for N in (10, 20, 40)]
+    full = errs("fullway", (0.1, 0.1), 1)
+    half = errs("halfway", (0.1, 0.1), 0)
+    half_slow = errs("halfway", (0.01, 0.01), 0)
+    full_fast = errs("fullway", (0.4, 0.4), 1)
+    for e in (full, half_slow, full_fast):
+        assert all(a / b > 12.0 for a, b in zip(e, e[1:])), e
+    assert half[0] < half[1] < half[2] and half[2] > 1.0, half

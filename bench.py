@@ -1,0 +1,361 @@
+#!/usr/bin/env python
+"""Throughput of the fourth-order BGK lattice Boltzmann hot path on D3Q19 256^3 (periodic).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--n 256]
+
+One benchmark step is one pass of the hot path over the workload: one lattice update of the FP64
+path, one of the FP32-deviation path and one adjoint update (FP32-deviation adjoint with the dL/dR
+accumulation), each a fused stream+collide kernel over all 256^3 nodes. `value` is the FP64 path's
+MLUPS (million lattice-node updates per second, whole job over N GPUs); the other forms are reported
+under "forms". Inputs are resident in HBM and each population buffer (2.5 GB) exceeds the 126 MB L2,
+so no L2 flush is needed between iterations. `e2e` times the same FP64 metric through the public API
+with host buffers: upload of phi0 and grad phi0 from pinned memory, init, 1000 steps (the workload's
+run length), macro and download of phi, per e2e step.
+
+Under torchrun (N > 1) every rank runs the workload on its own GPU (independent replicas: the path
+has no data exchange between boxes of one replica), timing is bracketed by a barrier and CUDA
+synchronisation on both sides, and rank 0 reports the max over ranks.
+
+--impl reference times the FP64 CPU oracle (the reference implementation of this paper-only
+repository) on the host cores, one oracle step of the same workload per benchmark step.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS & HBM GB/s (% of peak), D3Q19 256^3: FP64 vs FP32-mixed vs adjoint"
+UNIT = "MLUPS"
+U = (0.1, 0.1, 0.1)
+NMODES, SEED = 8, 2
+BYTES_PER_SITE = {"fp64": 2 * 19 * 8, "fp32dev": 2 * 19 * 4 + 16, "adjoint": 2 * 19 * 4 + 16 + 16}
+E2E_STEPS = 1000
+
+
+def workload(n):
+    return {"workload": "D3Q19 %d^3 periodic, 8 seeded Fourier modes (k in 1..3), u=(0.1,0.1,0.1), tau=0.5 (s=2), R=0" % n,
+            "lattice": "D3Q19", "n": n, "sites": n ** 3, "tau": 0.5, "u": list(U), "modes": NMODES,
+            "step": "one update of each form: fp64, fp32dev, adjoint(fp32dev, with dL/dR)",
+            "l2": "inputs larger than L2 (population buffers 2.5 GB / 1.3 GB)",
+            "e2e_job": "H2D phi0+grad (pinned), init, %d fp64 steps, macro, D2H phi" % E2E_STEPS}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            pk = json.load(fh)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def profiled_traffic(kernel_src: str):
+    """DRAM bytes per launch of the FP64 step kernel from the committed ncu summary, if the kernel
+    source is unchanged since the capture (the summary records the source hash)."""
+    path = os.path.join(ROOT, "profiles", "fp64_step_d3q19_256.md")
+    try:
+        txt = open(path).read()
+    except OSError:
+        return None
+    h = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()[:16]
+    want = None
+    for line in txt.splitlines():
+        if line.startswith("source_sha256_16:"):
+            want = line.split(":", 1)[1].strip()
+        if line.startswith("dram_bytes_per_launch:"):
+            val = float(line.split(":", 1)[1].strip())
+            return val if want == h else None
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu, self.lines, self.proc = gpu_index, [], None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.t.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup():
+    import torch
+
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    return ws, rank, local
+
+
+def barrier_max(x: float, ws: int) -> float:
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(ws: int):
+    import torch
+
+    torch.cuda.synchronize()
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+    torch.cuda.synchronize()
+
+
+def cpu_oracle_mlups(n: int, steps: int, threads: int):
+    from oracle import oracle as O
+    from paper_2410_13165_gb300 import workloads as W
+
+    O.set_threads(threads)
+    m = O.Model(3, n, 0.0, 1.0, U)
+    phi0, grad, _, _ = W.periodic_problem(3, n, NMODES, SEED)
+    f = m.init(phi0, grad, 3)
+    f = m.step(f, 0, 1)
+    t0 = time.perf_counter()
+    m.step(f, 1, steps)
+    dt = time.perf_counter() - t0
+    return n ** 3 * steps / dt / 1e6, dt
+
+
+def run_reference(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if int(os.environ.get("RANK", "0")) != 0:
+        return 0
+    from oracle import oracle as O
+    from paper_2410_13165_gb300 import workloads as W
+
+    threads = os.cpu_count() or 1
+    O.set_threads(threads)
+    n = args.n
+    m = O.Model(3, n, 0.0, 1.0, U)
+    phi0, grad, _, _ = W.periodic_problem(3, n, NMODES, SEED)
+    f = m.init(phi0, grad, 3)
+    f = m.step(f, 0, args.warmup)
+    t0 = time.perf_counter()
+    f = m.step(f, args.warmup, args.steps)
+    dt = time.perf_counter() - t0
+    mlups = n ** 3 * args.steps / dt / 1e6
+    line = {"metric": METRIC, "value": mlups, "unit": UNIT, "impl": "reference", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload(n),
+            "cpu_baseline": {"value": mlups, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": "FP64 CPU oracle, one step of the D3Q19 %d^3 workload per benchmark step" % n},
+            "e2e": {"value": mlups, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def run_ours(args):
+    import torch
+
+    from paper_2410_13165_gb300 import LBM, build
+    from paper_2410_13165_gb300 import workloads as W
+
+    ws, rank, local = dist_setup()
+    if ws == 1:
+        torch.cuda.set_device(0)
+    build.build()
+    n = args.n
+    S = n ** 3
+    phi0_np, grad_np, F, X = W.periodic_problem(3, n, NMODES, SEED)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    phi0 = torch.from_numpy(phi0_np).to(dev)
+    grad = torch.from_numpy(np.ascontiguousarray(grad_np).ravel()).to(dev)
+    del X
+
+    sims = {"fp64": LBM(3, n, u=U, tau=0.5), "fp32dev": LBM(3, n, u=U, tau=0.5, precision="fp32dev")}
+    adj = LBM(3, n, u=U, tau=0.5, precision="fp32dev")
+    for s in sims.values():
+        s.init(phi0, grad)
+    adj.init(phi0, grad)
+    adj.step(1)
+    adj.adjoint_seed(adj.macro())
+    stream = torch.cuda.current_stream()
+
+    def one_pass(ev=None):
+        if ev:
+            ev[0].record(stream)
+        sims["fp64"].step(1)
+        if ev:
+            ev[1].record(stream)
+        sims["fp32dev"].step(1)
+        if ev:
+            ev[2].record(stream)
+        adj.adjoint_step(1)
+        if ev:
+            ev[3].record(stream)
+
+    for _ in range(max(args.warmup, 3)):
+        one_pass()
+    K = args.steps
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(K)]
+    barrier(ws)
+    with ClockSampler(local) as clk:
+        t_start = torch.cuda.Event(enable_timing=True)
+        t_end = torch.cuda.Event(enable_timing=True)
+        t_start.record(stream)
+        for k in range(K):
+            one_pass(evs[k])
+        t_end.record(stream)
+        barrier(ws)
+    total_ms = t_start.elapsed_time(t_end)
+    per = {"fp64": 0.0, "fp32dev": 0.0, "adjoint": 0.0}
+    for k in range(K):
+        per["fp64"] += evs[k][0].elapsed_time(evs[k][1])
+        per["fp32dev"] += evs[k][1].elapsed_time(evs[k][2])
+        per["adjoint"] += evs[k][2].elapsed_time(evs[k][3])
+    per = {k: barrier_max(v / K, ws) for k, v in per.items()}
+    total_ms = barrier_max(total_ms, ws)
+    peak, peak_kind = measured_peaks()
+    forms = {}
+    for name, ms in per.items():
+        gbs = BYTES_PER_SITE[name] * S / (ms * 1e-3) / 1e9
+        forms[name] = {"mlups": ws * S / (ms * 1e-3) / 1e6, "ms_per_lb_step": ms, "gbs_per_gpu": gbs,
+                       "frac_of_hbm": gbs / peak, "bytes_per_site": BYTES_PER_SITE[name]}
+    fp64 = forms["fp64"]
+    kernel_src = os.path.join(ROOT, "paper_2410_13165_gb300", "csrc", "lhe_step_fp64.cu")
+    traffic = profiled_traffic(kernel_src)
+
+    # e2e through the public API with host buffers (FP64 path, whole job)
+    e2e = None
+    if args.e2e_steps > 0:
+        h_phi0 = torch.from_numpy(phi0_np).pin_memory()
+        h_grad = torch.from_numpy(np.ascontiguousarray(grad_np).ravel()).pin_memory()
+        h_out = torch.empty(S, dtype=torch.float64).pin_memory()
+        d_phi0 = torch.empty_like(phi0)
+        d_grad = torch.empty_like(grad)
+        sim = sims["fp64"]
+
+        def job():
+            d_phi0.copy_(h_phi0, non_blocking=True)
+            d_grad.copy_(h_grad, non_blocking=True)
+            sim.init(d_phi0, d_grad)
+            sim.step(E2E_STEPS)
+            h_out.copy_(sim.macro(), non_blocking=True)
+
+        job()
+        barrier(ws)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(args.e2e_steps):
+            job()
+        b.record(stream)
+        barrier(ws)
+        e2e_ms = barrier_max(a.elapsed_time(b) / args.e2e_steps, ws)
+        e2e = {"value": ws * S * E2E_STEPS / (e2e_ms * 1e-3) / 1e6, "unit": UNIT, "ms_per_job": e2e_ms,
+               "h2d_bytes_per_step": (h_phi0.numel() + h_grad.numel()) * 8, "d2h_bytes_per_step": h_out.numel() * 8,
+               "lb_steps_per_job": E2E_STEPS}
+
+    cpu = None
+    if rank == 0 and args.cpu_baseline:
+        threads = os.cpu_count() or 1
+        mlups, secs = cpu_oracle_mlups(args.cpu_n, args.cpu_steps, threads)
+        cpu = {"value": mlups, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": "FP64 CPU oracle, D3Q19 %d^3 sample of the workload, %d steps (%.1f s)" % (
+                   args.cpu_n, args.cpu_steps, secs)}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": fp64["mlups"], "unit": UNIT, "n_gpus": ws, "steps": K,
+                "warmup": max(args.warmup, 3), "ms_per_step": total_ms / K, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": dict(workload(n), parallelism="replicas" if ws > 1 else "single GPU"),
+                "forms": forms,
+                "roofline": {"bound": "hbm", "kernel": "k_step_fp64<3,fwd,periodic,s=2>",
+                             "achieved": fp64["gbs_per_gpu"], "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                             "frac": fp64["gbs_per_gpu"] / peak, "traffic": traffic,
+                             "algorithmic_bytes_per_launch": BYTES_PER_SITE["fp64"] * S},
+                "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 3 * K,
+                "clocks": clk.summary()}
+        print(json.dumps(line))
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=256)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--cpu-baseline", type=int, default=1)
+    ap.add_argument("--cpu-n", type=int, default=128)
+    ap.add_argument("--cpu-steps", type=int, default=40)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

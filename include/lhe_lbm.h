@@ -1,0 +1,208 @@
+/*
+ * lhe_lbm.h -- C ABI of the GB300 (sm_103a) library for the unified fourth-order BGK lattice
+ * Boltzmann model of the d-dimensional linear hyperbolic equation (L-HE)
+ *
+ *     d_t phi + u . grad phi = R,   phi(x, 0) = phi0(x),                       (Sec. 2.1, Eq. (HE))
+ *
+ * on the DdQ(2d^2+1) lattice with the fourth-order equilibrium moments of Chen, Chai & Shi,
+ * arXiv:2410.13165. Citations below name the paper's sections and equations.
+ *
+ * Conventions shared by every entry point
+ *   - All pointers named *_dev are CUDA device pointers; *_host are host pointers. The caller owns
+ *     every pointer it passes; the library never frees or retains them beyond the call, except
+ *     where stated. The library owns the population buffers it allocates in lhe_lbm_create().
+ *   - Every call is asynchronous on the handle's CUDA stream (params.stream, 0 = legacy default
+ *     stream) unless it says it synchronises. Device pointers must stay valid until the stream
+ *     has executed the call.
+ *   - Fields are laid out with x_1 fastest: site = i_1 + n_1*(i_2 + n_2*(...)), S = prod(n_i).
+ *     Vector fields (gradients) are component-major: v[i*S + site].
+ *   - Lattice: square, spacing dx; time step dt = dx / c (acoustic scaling, Sec. 2.2).
+ *       periodic : node i at lo + i dx,        dx = (hi - lo)/n
+ *       full-way : node i at lo + i dx,        dx = (hi - lo)/(n - 1)   (nodes on the faces)
+ *       half-way : node i at lo + (i + 1/2)dx, dx = (hi - lo)/n         (walls at mid-link)
+ *     (the lattice-point sets of Eq. (rmse)); dx must be equal in every dimension.
+ *   - Errors: every call returns an lhe_status; it never throws, traps or aborts the device.
+ *     A human-readable message is available from lhe_lbm_last_error(). Device-side errors that
+ *     are only known after kernels ran (non-finite values) surface at the next synchronising call.
+ *   - Thread safety: a handle must not be used from two host threads at once.
+ */
+#ifndef LHE_LBM_H
+#define LHE_LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define LHE_API __attribute__((visibility("default")))
+#else
+#define LHE_API
+#endif
+
+#define LHE_ABI_VERSION 1
+#define LHE_MAX_DIM 5   /* the entropy conditions need d < 6 (Proposition 1, Eq. (sigma=0)) */
+#define LHE_MAX_Q 51    /* 2 d^2 + 1 for d = 5 */
+#define LHE_MAX_MODES 16
+
+typedef struct lhe_lbm lhe_lbm; /* opaque handle */
+
+typedef enum {
+  LHE_OK = 0,
+  LHE_ERR_ARG = 1,       /* invalid argument (message says which) */
+  LHE_ERR_UNSTABLE = 2,  /* some EDF weight omega_k <= 0: not entropy stable (Sec. 4.1, Eq. (skfk)) */
+  LHE_ERR_CUDA = 3,      /* a CUDA runtime call or kernel launch failed */
+  LHE_ERR_OOM = 4,       /* device allocation failed */
+  LHE_ERR_NONFINITE = 5, /* a NaN or Inf was found in the state */
+  LHE_ERR_STATE = 6      /* call out of order (e.g. step before init) or unsupported combination */
+} lhe_status;
+
+typedef enum { LHE_BC_PERIODIC = 0, LHE_BC_FULLWAY = 1, LHE_BC_HALFWAY = 2 } lhe_bc_kind;
+
+/* LHE_FP64: populations stored and updated in FP64.
+ * LHE_FP32_DEV: populations stored as FP32 deviations g_k = f_k - omega_k phi from the local
+ * equilibrium, phi stored and accumulated in FP64 (the library's precision form; the paper is
+ * precision-agnostic). */
+typedef enum { LHE_FP64 = 0, LHE_FP32_DEV = 1 } lhe_precision;
+
+/* Fourth-order EDF moments m4_ij = m^{eq|4}_{x_i^2 x_j^2} (free after Eq. (third-condition-2)):
+ * LHE_M4_RULE     -- Eq. (meq-4rd) with parameter g (the paper's numerics use g = 1/2), equal for all pairs;
+ * LHE_M4_EXPLICIT -- m4[p] for the pairs i<j in lexicographic order, in units of c^4. */
+typedef enum { LHE_M4_RULE = 0, LHE_M4_EXPLICIT = 1 } lhe_m4_mode;
+
+typedef struct {
+  int32_t d;              /* spatial dimension, 1..5 */
+  int32_t bc;             /* lhe_bc_kind */
+  int32_t precision;      /* lhe_precision */
+  int32_t init_order;     /* 1: f = f^eq;  3: Eq. (ini-simp) (Sec. 3.2) */
+  int32_t bc_order;       /* full-way: 1, 3 or 4 (Eq. (bun1)); half-way: 1..4 (Eq. (bun2)); unused if periodic */
+  int32_t m4_mode;        /* lhe_m4_mode */
+  int32_t allow_unstable; /* nonzero: accept weights with omega_k <= 0 (otherwise LHE_ERR_UNSTABLE) */
+  int32_t reserved0;      /* must be 0 */
+  int64_t n[LHE_MAX_DIM]; /* nodes per dimension (first d used); full-way n >= 3, otherwise n >= 3 */
+  double lo[LHE_MAX_DIM]; /* box [lo, hi] per dimension */
+  double hi[LHE_MAX_DIM];
+  double c;               /* lattice velocity c = dx/dt > 0 (the paper's numerics use c = 1) */
+  double u[LHE_MAX_DIM];  /* transport velocity u of Eq. (HE) */
+  double R;               /* constant source R of Eq. (HE); see lhe_lbm_init for a per-site field */
+  double tau;             /* relaxation time, s = 1/tau (Eq. (BGK-LB-Evolution)); the paper's method: tau = 0.5 */
+  double g;               /* parameter of Eq. (meq-4rd), 0 < g < 1 */
+  double m4[10];          /* explicit m4_ij (LHE_M4_EXPLICIT) */
+  void *stream;           /* cudaStream_t used by every call on this handle (0 = default stream) */
+} lhe_lbm_params;
+
+/* Read-only description of a created handle. */
+typedef struct {
+  int32_t d, Q;            /* Q = 2 d^2 + 1 */
+  int64_t S;               /* number of lattice nodes */
+  int64_t n_boundary;      /* number of boundary nodes (Dirichlet), 0 if periodic */
+  int64_t step;            /* current time index: the state holds t_n = step * dt */
+  double dx, dt, s;        /* lattice spacing, time step, relaxation parameter */
+  double m4[10];           /* fourth moments used, pairs i<j (units of c^4) */
+  double omega[LHE_MAX_Q]; /* EDF weights omega_k (Eq. (omega_k-2)), f^eq_k = omega_k phi */
+  int32_t e[LHE_MAX_Q * LHE_MAX_DIM]; /* unit lattice vectors e[k*d + i] (c_k = c e_k), paper's order */
+  uint64_t state_bytes;    /* bytes of one forward state (see lhe_lbm_get_state) */
+} lhe_lbm_info_t;
+
+/* Dirichlet data phi = h on the boundary, taken from the exact-solution family
+ *   h(x, t) = b + R t + sum_i g_i (x_i - u_i t) + sum_m a_m sin(kappa_m . (x - u t) + theta_m),
+ * which solves Eq. (HE) for constant R. The boundary kernels evaluate it and the space-time
+ * derivatives the boundary schemes need on the device, at every step's time. */
+typedef struct {
+  int32_t nmodes;                            /* 0..LHE_MAX_MODES */
+  int32_t reserved0;                         /* must be 0 */
+  double b;
+  double g[LHE_MAX_DIM];
+  double a[LHE_MAX_MODES];
+  double kappa[LHE_MAX_MODES * LHE_MAX_DIM]; /* kappa[m*LHE_MAX_DIM + i] */
+  double theta[LHE_MAX_MODES];
+} lhe_wave;
+
+/* Library version of this header (LHE_ABI_VERSION) and sizeof(lhe_lbm_params), for bindings
+ * to check their struct layout. */
+LHE_API int32_t lhe_lbm_abi_version(void);
+LHE_API uint64_t lhe_lbm_params_size(void);
+
+/* Fill *p with defaults: d = 3, periodic, FP64, init_order 3, bc_order 4, m4 rule with g = 1/2,
+ * c = 1, tau = 0.5, R = 0, u = 0, n = 16, box [0,1]^d, default stream. */
+LHE_API lhe_status lhe_lbm_default_params(lhe_lbm_params *p);
+
+/* Compute the model without allocating device memory: m4 (Eq. (meq-4rd) or explicit), the EDF
+ * weights omega (Eq. (omega_k-2)) and the lattice vectors. omega_host (Q doubles), m4_host
+ * (d(d-1)/2 doubles) and e_host (Q*d int32) may each be NULL. Returns LHE_ERR_UNSTABLE when some
+ * omega_k <= 0 (the arrays are still filled). */
+LHE_API lhe_status lhe_lbm_model(const lhe_lbm_params *p, double *omega_host, double *m4_host, int32_t *e_host,
+                         int32_t *Q_out);
+
+/* Validate params, compute the model (as lhe_lbm_model), allocate two population buffers on the
+ * current CUDA device (plus the boundary-node list for Dirichlet boxes) and return a handle.
+ * Errors: LHE_ERR_ARG, LHE_ERR_UNSTABLE (unless allow_unstable), LHE_ERR_OOM, LHE_ERR_CUDA.
+ * On error *out is NULL and lhe_lbm_last_error(NULL) holds the message. */
+LHE_API lhe_status lhe_lbm_create(const lhe_lbm_params *p, lhe_lbm **out);
+
+/* Synchronise the handle's stream and free everything the handle owns. NULL is accepted. */
+LHE_API lhe_status lhe_lbm_destroy(lhe_lbm *lbm);
+
+/* Message of the last failed call on this handle; with NULL, of the last failed create/model
+ * call on this thread. The string lives until the next failing call. */
+LHE_API const char *lhe_lbm_last_error(const lhe_lbm *lbm);
+
+/* Fill *info (host). */
+LHE_API lhe_status lhe_lbm_info(const lhe_lbm *lbm, lhe_lbm_info_t *info);
+
+/* Replace the CUDA stream used by subsequent calls. */
+LHE_API lhe_status lhe_lbm_set_stream(lhe_lbm *lbm, void *stream);
+
+/* Initialise the state at t = 0 (step index 0) from phi0_dev (S doubles):
+ *   init_order 3: f_k(x,0) = omega_k [phi0 + (dt/2)(u - c_k) . grad phi0]    Eq. (ini-simp)
+ *   init_order 1: f_k(x,0) = omega_k phi0                                     (f = f^eq)
+ * grad_dev: d*S doubles (component-major), or NULL, in which case the gradient is the periodic
+ * fourth-order central difference of phi0 (periodic boxes only; LHE_ERR_ARG otherwise).
+ * R_dev: per-site source R(x) (S doubles; the discrete source is R_k = omega_k R(x)), or NULL for
+ * the constant params.R. The field is copied; Dirichlet boxes require R_dev == NULL.
+ * The library stores post-collision populations internally, so init also applies one collision. */
+LHE_API lhe_status lhe_lbm_init(lhe_lbm *lbm, const double *phi0_dev, const double *grad_dev, const double *R_dev);
+
+/* Set the Dirichlet data (copied). Required before lhe_lbm_step on a full-way or half-way box. */
+LHE_API lhe_status lhe_lbm_set_boundary_wave(lhe_lbm *lbm, const lhe_wave *w_host);
+
+/* Advance n >= 0 time steps of Eq. (BGK-LB-Evolution) (collide with s = 1/tau, stream), with
+ * the full-way (Eq. (bun1)) or half-way (Eq. (bun2)) scheme for the unknown populations of the
+ * boundary nodes of a Dirichlet box. Errors: LHE_ERR_STATE before init / without boundary data. */
+LHE_API lhe_status lhe_lbm_step(lhe_lbm *lbm, int64_t n);
+
+/* Macroscopic variable phi(x, t_step) = sum_k f_k (Eq. (0-1-meq)) into phi_dev (S doubles). */
+LHE_API lhe_status lhe_lbm_macro(lhe_lbm *lbm, double *phi_dev);
+
+/* Synchronising diagnostics of the current state, into out_host[4]:
+ *   [0] sum_x phi (mass), [1] sum_x sum_k f_k^2 / (2 omega_k) (total kinetic entropy, Eq. (skfk)),
+ *   [2] max_x |phi|, [3] number of non-finite populations.
+ * Returns LHE_ERR_NONFINITE when [3] > 0. */
+LHE_API lhe_status lhe_lbm_diagnostics(lhe_lbm *lbm, double *out_host);
+
+/* Copy the forward state (post-collision populations, and phi for LHE_FP32_DEV) to/from a
+ * caller buffer of info.state_bytes bytes (device or host memory; cudaMemcpyKind default), for
+ * checkpoint/restart. set_state also sets the step index. */
+LHE_API lhe_status lhe_lbm_get_state(lhe_lbm *lbm, void *buf);
+LHE_API lhe_status lhe_lbm_set_state(lhe_lbm *lbm, const void *buf, int64_t step);
+
+/* ---------------- discrete adjoint (periodic boxes) ----------------
+ * The scheme is affine in the populations, so its adjoint needs no forward state: given the
+ * cotangent dL/dphi(t_T) of any loss L of the final field, lhe_lbm_adjoint_seed() sets the
+ * adjoint state, each lhe_lbm_adjoint_step() applies the transpose of one step (reverse stream,
+ * transposed collision) and accumulates dL/dR(x), and lhe_lbm_adjoint_grads() applies the
+ * transpose of the initialisation. The adjoint uses the handle's precision and allocates its own
+ * buffers on first use. */
+LHE_API lhe_status lhe_lbm_adjoint_seed(lhe_lbm *lbm, const double *dL_dphiT_dev);
+LHE_API lhe_status lhe_lbm_adjoint_step(lhe_lbm *lbm, int64_t n);
+/* dL/dphi0 (S doubles), dL/d(grad phi0) (d*S doubles, only meaningful when lhe_lbm_init got an
+ * explicit gradient; NULL to skip), dL/dR(x) (S doubles, NULL to skip). When init used the
+ * finite-difference gradient, its transpose is folded into dL/dphi0. */
+LHE_API lhe_status lhe_lbm_adjoint_grads(lhe_lbm *lbm, double *dL_dphi0_dev, double *dL_dgrad_dev, double *dL_dR_dev);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LHE_LBM_H */

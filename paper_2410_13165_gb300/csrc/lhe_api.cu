@@ -1,0 +1,627 @@
+// lhe_api.cu -- host implementation of the C ABI declared in include/lhe_lbm.h.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "lhe_internal.h"
+
+using namespace lhe;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+lhe_status fail(lhe_lbm *lbm, lhe_status st, const std::string &msg) {
+  if (lbm) lbm->err = msg;
+  else g_last_error = msg;
+  return st;
+}
+
+lhe_status cuda_fail(lhe_lbm *lbm, cudaError_t e, const char *what) {
+  std::string msg = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+  return fail(lbm, e == cudaErrorMemoryAllocation ? LHE_ERR_OOM : LHE_ERR_CUDA, msg);
+}
+
+#define LHE_CK(lbm, call)                                    \
+  do {                                                       \
+    cudaError_t e_ = (call);                                 \
+    if (e_ != cudaSuccess) return cuda_fail(lbm, e_, #call); \
+  } while (0)
+
+// Lattice vectors of the paper's DdQ(2d^2+1) ordering (same construction as the device tables).
+int lattice_vectors(int d, int32_t *e) {
+  switch (d) {
+    case 1: { constexpr Lattice<1> L{}; for (int k = 0; k < L.Q; ++k) for (int i = 0; i < 1; ++i) e[k * d + i] = L.e[k][i]; return L.Q; }
+    case 2: { constexpr Lattice<2> L{}; for (int k = 0; k < L.Q; ++k) for (int i = 0; i < 2; ++i) e[k * d + i] = L.e[k][i]; return L.Q; }
+    case 3: { constexpr Lattice<3> L{}; for (int k = 0; k < L.Q; ++k) for (int i = 0; i < 3; ++i) e[k * d + i] = L.e[k][i]; return L.Q; }
+    case 4: { constexpr Lattice<4> L{}; for (int k = 0; k < L.Q; ++k) for (int i = 0; i < 4; ++i) e[k * d + i] = L.e[k][i]; return L.Q; }
+    case 5: { constexpr Lattice<5> L{}; for (int k = 0; k < L.Q; ++k) for (int i = 0; i < 5; ++i) e[k * d + i] = L.e[k][i]; return L.Q; }
+    default: return -1;
+  }
+}
+
+// Eq. (meq-4rd) in units of c^4 with sigma = u / c: g * max{lower bounds} + (1 - g) * min{upper bounds},
+// the bounds being those of Eq. (psi-4-equal) (equal fourth moments for every pair).
+double m4_rule(int d, const double *sig, double g) {
+  if (d < 2) return 0.0;
+  double ss = 0.0;
+  for (int i = 0; i < d; ++i) ss += sig[i] * sig[i];
+  double lower = (2.0 * d - 6.0 + 4.0 * ss) / (3.0 * d * (d - 1));
+  for (int i = 0; i < d; ++i)
+    for (int j = i + 1; j < d; ++j) {
+      lower = std::fmax(lower, (std::fabs(sig[i] + sig[j]) - 2.0 * sig[i] * sig[j]) / 3.0);
+      lower = std::fmax(lower, (std::fabs(sig[i] - sig[j]) + 2.0 * sig[i] * sig[j]) / 3.0);
+    }
+  double upper = INFINITY;
+  for (int i = 0; i < d; ++i)
+    upper = std::fmin(upper, (1.0 + 2.0 * sig[i] * sig[i] - std::fabs((4.0 - d) * sig[i])) / (3.0 * (d - 1)));
+  return g * lower + (1.0 - g) * upper;
+}
+
+// Eq. (omega_k-2) (units c = 1, sigma = u/c) for per-pair fourth moments m4[p], p over i<j.
+void weights(int d, const int32_t *e, int Q, const double *sig, const double *m4, double *omega) {
+  int pidx[kMaxD][kMaxD] = {};
+  int p = 0;
+  double m4sum = 0.0, ss = 0.0;
+  for (int i = 0; i < d; ++i)
+    for (int j = i + 1; j < d; ++j) {
+      pidx[i][j] = pidx[j][i] = p;
+      m4sum += m4[p++];
+    }
+  for (int i = 0; i < d; ++i) ss += sig[i] * sig[i];
+  for (int k = 0; k < Q; ++k) {
+    int ax[2] = {-1, -1}, nz = 0;
+    for (int i = 0; i < d; ++i)
+      if (e[k * d + i]) ax[nz++] = i;
+    if (nz == 0) {
+      omega[k] = (3.0 - d - 2.0 * ss + 3.0 * m4sum) / 3.0;
+    } else if (nz == 1) {
+      const int i = ax[0];
+      double row = 0.0;
+      for (int j = 0; j < d; ++j)
+        if (j != i) row += m4[pidx[i][j]];
+      omega[k] = (e[k * d + i] * (4.0 - d) * sig[i] + 1.0 + 2.0 * sig[i] * sig[i] - 3.0 * row) / 6.0;
+    } else {
+      const int i = ax[0], j = ax[1];
+      const double si = e[k * d + i], sj = e[k * d + j];
+      omega[k] = (3.0 * m4[pidx[i][j]] + 2.0 * si * sj * sig[i] * sig[j] + si * sig[i] + sj * sig[j]) / 12.0;
+    }
+  }
+}
+
+struct Model {
+  int Q = 0;
+  double dx = 0, dt = 0, s = 0;
+  double x0[kMaxD] = {};
+  double m4[10] = {};
+  double omega[kMaxQ] = {};
+  int32_t e[kMaxQ * kMaxD] = {};
+  bool stable = true;
+};
+
+lhe_status build_model(const lhe_lbm_params *p, Model &m, lhe_lbm *err_to) {
+  if (!p) return fail(err_to, LHE_ERR_ARG, "params is NULL");
+  const int d = p->d;
+  if (d < 1 || d > kMaxD) return fail(err_to, LHE_ERR_ARG, "d must be in 1..5");
+  if (p->bc < 0 || p->bc > 2) return fail(err_to, LHE_ERR_ARG, "bc must be LHE_BC_PERIODIC, LHE_BC_FULLWAY or LHE_BC_HALFWAY");
+  if (p->precision != LHE_FP64 && p->precision != LHE_FP32_DEV) return fail(err_to, LHE_ERR_ARG, "unknown precision");
+  if (p->init_order != 1 && p->init_order != 3) return fail(err_to, LHE_ERR_ARG, "init_order must be 1 or 3");
+  if (p->bc == LHE_BC_FULLWAY && p->bc_order != 1 && p->bc_order != 3 && p->bc_order != 4)
+    return fail(err_to, LHE_ERR_ARG, "full-way bc_order must be 1, 3 or 4");
+  if (p->bc == LHE_BC_HALFWAY && (p->bc_order < 1 || p->bc_order > 4))
+    return fail(err_to, LHE_ERR_ARG, "half-way bc_order must be 1..4");
+  if (!(p->c > 0.0) || !std::isfinite(p->c)) return fail(err_to, LHE_ERR_ARG, "c must be positive");
+  if (!(p->tau > 0.0) || !std::isfinite(p->tau)) return fail(err_to, LHE_ERR_ARG, "tau must be positive");
+  if (p->reserved0 != 0) return fail(err_to, LHE_ERR_ARG, "reserved0 must be 0");
+  if (p->m4_mode != LHE_M4_RULE && p->m4_mode != LHE_M4_EXPLICIT) return fail(err_to, LHE_ERR_ARG, "unknown m4_mode");
+  if (p->m4_mode == LHE_M4_RULE && !(p->g >= 0.0 && p->g <= 1.0)) return fail(err_to, LHE_ERR_ARG, "g must be in [0, 1]");
+  double dxs[kMaxD];
+  for (int i = 0; i < d; ++i) {
+    if (p->n[i] < 3) return fail(err_to, LHE_ERR_ARG, "every n[i] must be >= 3");
+    if (!(p->hi[i] > p->lo[i])) return fail(err_to, LHE_ERR_ARG, "every hi[i] must exceed lo[i]");
+    if (!std::isfinite(p->u[i])) return fail(err_to, LHE_ERR_ARG, "u must be finite");
+    const double span = (p->bc == LHE_BC_FULLWAY) ? (double)(p->n[i] - 1) : (double)p->n[i];
+    dxs[i] = (p->hi[i] - p->lo[i]) / span;
+  }
+  for (int i = 1; i < d; ++i)
+    if (std::fabs(dxs[i] - dxs[0]) > 1e-12 * dxs[0])
+      return fail(err_to, LHE_ERR_ARG, "the lattice must be square: (hi-lo)/n (or /(n-1) for full-way) must agree in every dimension");
+  if (!std::isfinite(p->R)) return fail(err_to, LHE_ERR_ARG, "R must be finite");
+  m.dx = dxs[0];
+  m.dt = m.dx / p->c;
+  m.s = 1.0 / p->tau;
+  for (int i = 0; i < d; ++i) m.x0[i] = p->lo[i] + (p->bc == LHE_BC_HALFWAY ? 0.5 * m.dx : 0.0);
+  m.Q = lattice_vectors(d, m.e);
+  double sig[kMaxD];
+  for (int i = 0; i < d; ++i) sig[i] = p->u[i] / p->c;
+  const int npairs = d * (d - 1) / 2;
+  if (p->m4_mode == LHE_M4_RULE) {
+    const double v = m4_rule(d, sig, p->g);
+    for (int q = 0; q < npairs; ++q) m.m4[q] = v;
+  } else {
+    for (int q = 0; q < npairs; ++q) m.m4[q] = p->m4[q];
+  }
+  weights(d, m.e, m.Q, sig, m.m4, m.omega);
+  m.stable = true;
+  for (int k = 0; k < m.Q; ++k)
+    if (!(m.omega[k] > 0.0)) m.stable = false;
+  return LHE_OK;
+}
+
+Geom make_geom(int d, const int64_t *n) {
+  Geom g;
+  g.d = d;
+  int64_t stride = 1, si = 1;
+  for (int i = 0; i < d; ++i) {
+    g.n[i] = (int32_t)n[i];
+    g.stride[i] = (int32_t)stride;
+    g.dv[i] = FastDiv((uint32_t)n[i]);
+    g.dvi[i] = FastDiv((uint32_t)(n[i] - 2));
+    stride *= n[i];
+    si *= (n[i] - 2);
+  }
+  g.S = stride;
+  g.S_interior = si;
+  return g;
+}
+
+size_t pop_bytes(const lhe_lbm *l) {
+  return (size_t)l->Q * (size_t)l->g.S * (l->p.precision == LHE_FP64 ? sizeof(double) : sizeof(float));
+}
+
+StepArgs step_args(const lhe_lbm *l) {
+  StepArgs a{};
+  a.g = l->g;
+  for (int k = 0; k < l->Q; ++k) {
+    a.omega[k] = l->omega[k];
+    a.omega_f[k] = (float)l->omega[k];
+    a.dtwR_f[k] = (float)(l->dt * l->omega[k] * l->R);
+  }
+  a.s = l->s;
+  a.oms = 1.0 - l->s;
+  a.dtR = l->dt * l->R;
+  a.dt = l->dt;
+  a.Rfield = l->Rfield;
+  return a;
+}
+
+lhe_status check_handle(lhe_lbm *l) {
+  if (!l) return fail(nullptr, LHE_ERR_ARG, "handle is NULL");
+  return LHE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int32_t lhe_lbm_abi_version(void) { return LHE_ABI_VERSION; }
+uint64_t lhe_lbm_params_size(void) { return sizeof(lhe_lbm_params); }
+
+lhe_status lhe_lbm_default_params(lhe_lbm_params *p) {
+  if (!p) return fail(nullptr, LHE_ERR_ARG, "params is NULL");
+  std::memset(p, 0, sizeof(*p));
+  p->d = 3;
+  p->bc = LHE_BC_PERIODIC;
+  p->precision = LHE_FP64;
+  p->init_order = 3;
+  p->bc_order = 4;
+  p->m4_mode = LHE_M4_RULE;
+  for (int i = 0; i < LHE_MAX_DIM; ++i) {
+    p->n[i] = 16;
+    p->lo[i] = 0.0;
+    p->hi[i] = 1.0;
+  }
+  p->c = 1.0;
+  p->tau = 0.5;
+  p->g = 0.5;
+  return LHE_OK;
+}
+
+lhe_status lhe_lbm_model(const lhe_lbm_params *p, double *omega_host, double *m4_host, int32_t *e_host,
+                         int32_t *Q_out) {
+  Model m;
+  const lhe_status st = build_model(p, m, nullptr);
+  if (st != LHE_OK) return st;
+  if (omega_host) std::memcpy(omega_host, m.omega, sizeof(double) * m.Q);
+  if (m4_host) std::memcpy(m4_host, m.m4, sizeof(double) * (p->d * (p->d - 1) / 2));
+  if (e_host) std::memcpy(e_host, m.e, sizeof(int32_t) * m.Q * p->d);
+  if (Q_out) *Q_out = m.Q;
+  if (!m.stable) return fail(nullptr, LHE_ERR_UNSTABLE, "some EDF weight omega_k <= 0: the fourth moments violate the entropy-stability conditions (Proposition 1)");
+  return LHE_OK;
+}
+
+lhe_status lhe_lbm_create(const lhe_lbm_params *p, lhe_lbm **out) {
+  if (!out) return fail(nullptr, LHE_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  Model m;
+  lhe_status st = build_model(p, m, nullptr);
+  if (st != LHE_OK) return st;
+  if (!m.stable && !p->allow_unstable)
+    return fail(nullptr, LHE_ERR_UNSTABLE, "some EDF weight omega_k <= 0: not entropy stable (Proposition 1); set allow_unstable to proceed");
+  int64_t S = 1;
+  for (int i = 0; i < p->d; ++i) {
+    if (p->n[i] > (int64_t)INT32_MAX) return fail(nullptr, LHE_ERR_ARG, "n[i] too large");
+    S *= p->n[i];
+    if (S > (int64_t)INT32_MAX) return fail(nullptr, LHE_ERR_ARG, "the lattice has more than 2^31-1 nodes");
+  }
+  lhe_lbm *l = new (std::nothrow) lhe_lbm();
+  if (!l) return fail(nullptr, LHE_ERR_OOM, "host allocation failed");
+  l->p = *p;
+  l->Q = m.Q;
+  l->dx = m.dx;
+  l->dt = m.dt;
+  l->s = m.s;
+  l->R = p->R;
+  std::memcpy(l->omega, m.omega, sizeof(m.omega));
+  std::memcpy(l->m4, m.m4, sizeof(m.m4));
+  std::memcpy(l->e, m.e, sizeof(m.e));
+  std::memcpy(l->x0, m.x0, sizeof(m.x0));
+  l->g = make_geom(p->d, p->n);
+  l->stream = static_cast<cudaStream_t>(p->stream);
+  auto bail = [&](lhe_status s2) {
+    g_last_error = l->err;
+    lhe_lbm_destroy(l);
+    return s2;
+  };
+  const size_t pb = pop_bytes(l);
+  for (int b = 0; b < 2; ++b) {
+    cudaError_t e = cudaMalloc(&l->pop[b], pb);
+    if (e != cudaSuccess) return bail(cuda_fail(l, e, "cudaMalloc(populations)"));
+    if (p->precision == LHE_FP32_DEV) {
+      e = cudaMalloc(&l->phi[b], sizeof(double) * (size_t)S);
+      if (e != cudaSuccess) return bail(cuda_fail(l, e, "cudaMalloc(phi)"));
+    }
+  }
+  l->red_blocks = 152 * 4;
+  cudaError_t e = cudaMalloc(&l->red_partials, sizeof(double) * 4 * (size_t)l->red_blocks + sizeof(double) * 4);
+  if (e != cudaSuccess) return bail(cuda_fail(l, e, "cudaMalloc(reduction scratch)"));
+  l->red_out = l->red_partials + 4 * (size_t)l->red_blocks;
+  if (p->bc != LHE_BC_PERIODIC) {
+    std::vector<int32_t> sites;
+    sites.reserve((size_t)(S - l->g.S_interior));
+    for (int64_t s = 0; s < S; ++s) {
+      int64_t r = s;
+      bool bnd = false;
+      for (int i = 0; i < p->d; ++i) {
+        const int64_t xi = r % p->n[i];
+        r /= p->n[i];
+        if (xi == 0 || xi == p->n[i] - 1) bnd = true;
+      }
+      if (bnd) sites.push_back((int32_t)s);
+    }
+    l->nb = (int64_t)sites.size();
+    e = cudaMalloc(&l->bsites, sizeof(int32_t) * sites.size());
+    if (e != cudaSuccess) return bail(cuda_fail(l, e, "cudaMalloc(boundary nodes)"));
+    e = cudaMemcpy(l->bsites, sites.data(), sizeof(int32_t) * sites.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return bail(cuda_fail(l, e, "cudaMemcpy(boundary nodes)"));
+    e = cudaMalloc(&l->bc_table, sizeof(double) * ((size_t)kMaxModes * kMaxQ * 3 + kMaxModes));
+    if (e != cudaSuccess) return bail(cuda_fail(l, e, "cudaMalloc(boundary table)"));
+  }
+  *out = l;
+  return LHE_OK;
+}
+
+lhe_status lhe_lbm_destroy(lhe_lbm *l) {
+  if (!l) return LHE_OK;
+  cudaStreamSynchronize(l->stream);
+  for (int b = 0; b < 2; ++b) {
+    cudaFree(l->pop[b]);
+    cudaFree(l->phi[b]);
+    cudaFree(l->adj[b]);
+    cudaFree(l->adjW[b]);
+  }
+  cudaFree(l->gR);
+  cudaFree(l->Rfield);
+  cudaFree(l->fdgrad);
+  cudaFree(l->bsites);
+  cudaFree(l->bc_table);
+  cudaFree(l->red_partials);
+  delete l;
+  return LHE_OK;
+}
+
+const char *lhe_lbm_last_error(const lhe_lbm *l) { return l ? l->err.c_str() : g_last_error.c_str(); }
+
+lhe_status lhe_lbm_info(const lhe_lbm *l, lhe_lbm_info_t *info) {
+  if (!l || !info) return fail(nullptr, LHE_ERR_ARG, "NULL argument");
+  std::memset(info, 0, sizeof(*info));
+  info->d = l->p.d;
+  info->Q = l->Q;
+  info->S = l->g.S;
+  info->n_boundary = l->nb;
+  info->step = l->step;
+  info->dx = l->dx;
+  info->dt = l->dt;
+  info->s = l->s;
+  std::memcpy(info->m4, l->m4, sizeof(l->m4));
+  std::memcpy(info->omega, l->omega, sizeof(double) * l->Q);
+  std::memcpy(info->e, l->e, sizeof(int32_t) * l->Q * l->p.d);
+  info->state_bytes = pop_bytes(l) + (l->p.precision == LHE_FP32_DEV ? sizeof(double) * (size_t)l->g.S : 0);
+  return LHE_OK;
+}
+
+lhe_status lhe_lbm_set_stream(lhe_lbm *l, void *stream) {
+  if (lhe_status s = check_handle(l)) return s;
+  l->stream = static_cast<cudaStream_t>(stream);
+  return LHE_OK;
+}
+
+lhe_status lhe_lbm_init(lhe_lbm *l, const double *phi0, const double *grad, const double *Rf) {
+  if (lhe_status s = check_handle(l)) return s;
+  if (!phi0) return fail(l, LHE_ERR_ARG, "phi0 is NULL");
+  const int d = l->p.d;
+  const size_t S = (size_t)l->g.S;
+  if (Rf && l->p.bc != LHE_BC_PERIODIC)
+    return fail(l, LHE_ERR_ARG, "a per-site source field is only supported on periodic boxes (the boundary schemes assume constant R)");
+  if (!grad && l->p.init_order == 3 && l->p.bc != LHE_BC_PERIODIC)
+    return fail(l, LHE_ERR_ARG, "Dirichlet boxes need an explicit grad phi0 for the third-order initialisation");
+  if (Rf) {
+    if (!l->Rfield) LHE_CK(l, cudaMalloc(&l->Rfield, sizeof(double) * S));
+    LHE_CK(l, cudaMemcpyAsync(l->Rfield, Rf, sizeof(double) * S, cudaMemcpyDefault, l->stream));
+  } else if (l->Rfield) {
+    LHE_CK(l, cudaFree(l->Rfield));
+    l->Rfield = nullptr;
+  }
+  const double *gptr = grad;
+  l->grad_was_fd = false;
+  if (!grad && l->p.init_order == 3) {
+    if (!l->fdgrad) LHE_CK(l, cudaMalloc(&l->fdgrad, sizeof(double) * S * d));
+    LHE_CK(l, launch_fd_grad(d, l->g, l->dx, phi0, l->fdgrad, l->stream));
+    gptr = l->fdgrad;
+    l->grad_was_fd = true;
+  }
+  InitArgs a{};
+  a.g = l->g;
+  a.phi0 = phi0;
+  a.grad = gptr;
+  a.Rfield = l->Rfield;
+  a.dst = l->pop[0];
+  a.phi_dst = l->phi[0];
+  for (int k = 0; k < l->Q; ++k) a.omega[k] = l->omega[k];
+  a.s = l->s;
+  a.oms = 1.0 - l->s;
+  a.dt = l->dt;
+  a.dtR = l->dt * l->R;
+  a.c = l->p.c;
+  for (int i = 0; i < d; ++i) a.u[i] = l->p.u[i];
+  a.order = l->p.init_order;
+  l->init_order_used = l->p.init_order;
+  LHE_CK(l, launch_init(d, l->p.precision == LHE_FP32_DEV, a, l->stream));
+  l->cur = 0;
+  l->step = 0;
+  l->initialised = true;
+  l->adj_ready = false;
+  return LHE_OK;
+}
+
+lhe_status lhe_lbm_set_boundary_wave(lhe_lbm *l, const lhe_wave *w) {
+  if (lhe_status s = check_handle(l)) return s;
+  if (!w) return fail(l, LHE_ERR_ARG, "wave is NULL");
+  if (l->p.bc == LHE_BC_PERIODIC) return fail(l, LHE_ERR_STATE, "boundary data on a periodic box");
+  if (w->nmodes < 0 || w->nmodes > kMaxModes || w->reserved0 != 0) return fail(l, LHE_ERR_ARG, "nmodes must be in 0..16");
+  const int d = l->p.d, Q = l->Q;
+  std::vector<double> tab((size_t)w->nmodes * Q * 3 + w->nmodes);
+  for (int m = 0; m < w->nmodes; ++m) {
+    double ku = 0.0;
+    for (int i = 0; i < d; ++i) ku += w->kappa[m * LHE_MAX_DIM + i] * l->p.u[i];
+    tab[(size_t)w->nmodes * Q * 3 + m] = ku;
+    for (int k = 0; k < Q; ++k) {
+      double ke = 0.0;
+      for (int i = 0; i < d; ++i) ke += w->kappa[m * LHE_MAX_DIM + i] * l->e[k * d + i];
+      const double alpha = 0.5 * l->dx * ke;
+      tab[(m * Q + k) * 3 + 0] = l->p.c * ke;
+      tab[(m * Q + k) * 3 + 1] = std::cos(alpha);
+      tab[(m * Q + k) * 3 + 2] = std::sin(alpha);
+    }
+  }
+  LHE_CK(l, cudaStreamSynchronize(l->stream));
+  if (!tab.empty()) LHE_CK(l, cudaMemcpy(l->bc_table, tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice));
+  l->wave = *w;
+  l->have_wave = true;
+  return LHE_OK;
+}
+
+static BoundaryArgs boundary_args(const lhe_lbm *l) {
+  BoundaryArgs b{};
+  b.g = l->g;
+  b.sites = l->bsites;
+  b.nsites = l->nb;
+  b.table = l->bc_table;
+  for (int k = 0; k < l->Q; ++k) b.omega[k] = l->omega[k];
+  b.s = l->s;
+  b.oms = 1.0 - l->s;
+  b.R = l->R;
+  b.dt = l->dt;
+  b.dx = l->dx;
+  b.c = l->p.c;
+  for (int i = 0; i < l->p.d; ++i) {
+    b.x0[i] = l->x0[i];
+    b.u[i] = l->p.u[i];
+  }
+  b.order = l->p.bc_order;
+  b.nmodes = l->wave.nmodes;
+  b.b = l->wave.b;
+  for (int i = 0; i < kMaxD; ++i) b.gl[i] = l->wave.g[i];
+  for (int m = 0; m < kMaxModes; ++m) {
+    b.a[m] = l->wave.a[m];
+    b.theta[m] = l->wave.theta[m];
+    for (int i = 0; i < kMaxD; ++i) b.kappa[m * kMaxD + i] = l->wave.kappa[m * LHE_MAX_DIM + i];
+  }
+  return b;
+}
+
+lhe_status lhe_lbm_step(lhe_lbm *l, int64_t n) {
+  if (lhe_status s = check_handle(l)) return s;
+  if (n < 0) return fail(l, LHE_ERR_ARG, "n must be >= 0");
+  if (!l->initialised) return fail(l, LHE_ERR_STATE, "lhe_lbm_step before lhe_lbm_init");
+  const bool periodic = l->p.bc == LHE_BC_PERIODIC;
+  if (!periodic && !l->have_wave) return fail(l, LHE_ERR_STATE, "Dirichlet box without boundary data (lhe_lbm_set_boundary_wave)");
+  const int d = l->p.d;
+  const bool dev = l->p.precision == LHE_FP32_DEV;
+  StepArgs a = step_args(l);
+  BoundaryArgs b{};
+  if (!periodic) b = boundary_args(l);
+  for (int64_t it = 0; it < n; ++it) {
+    a.src = l->pop[l->cur];
+    a.dst = l->pop[1 - l->cur];
+    a.phi_src = l->phi[l->cur];
+    a.phi_dst = l->phi[1 - l->cur];
+    a.nwork = periodic ? l->g.S : l->g.S_interior;
+    cudaError_t e = dev ? launch_step_dev(d, false, !periodic, a, l->stream)
+                        : launch_step_fp64(d, false, !periodic, a, l->stream);
+    if (e != cudaSuccess) return cuda_fail(l, e, "step kernel launch");
+    if (!periodic) {
+      b.src = a.src;
+      b.dst = a.dst;
+      b.phi_src = a.phi_src;
+      b.phi_dst = a.phi_dst;
+      b.t_eval = (double)(l->p.bc == LHE_BC_FULLWAY ? l->step + 1 : l->step) * l->dt;
+      e = launch_boundary(d, l->p.bc, dev, b, l->stream);
+      if (e != cudaSuccess) return cuda_fail(l, e, "boundary kernel launch");
+    }
+    l->cur ^= 1;
+    l->step += 1;
+  }
+  return LHE_OK;
+}
+
+lhe_status lhe_lbm_macro(lhe_lbm *l, double *phi_out) {
+  if (lhe_status s = check_handle(l)) return s;
+  if (!phi_out) return fail(l, LHE_ERR_ARG, "phi_out is NULL");
+  if (!l->initialised) return fail(l, LHE_ERR_STATE, "lhe_lbm_macro before lhe_lbm_init");
+  if (l->p.precision == LHE_FP32_DEV) {
+    LHE_CK(l, cudaMemcpyAsync(phi_out, l->phi[l->cur], sizeof(double) * (size_t)l->g.S, cudaMemcpyDefault, l->stream));
+    return LHE_OK;
+  }
+  StepArgs a = step_args(l);
+  a.src = l->pop[l->cur];
+  LHE_CK(l, launch_macro_fp64(l->p.d, a, phi_out, l->stream));
+  return LHE_OK;
+}
+
+lhe_status lhe_lbm_diagnostics(lhe_lbm *l, double *out_host) {
+  if (lhe_status s = check_handle(l)) return s;
+  if (!out_host) return fail(l, LHE_ERR_ARG, "out_host is NULL");
+  if (!l->initialised) return fail(l, LHE_ERR_STATE, "lhe_lbm_diagnostics before lhe_lbm_init");
+  ReduceArgs a{};
+  a.g = l->g;
+  a.pop = l->pop[l->cur];
+  a.phi = l->phi[l->cur];
+  a.Rfield = l->Rfield;
+  for (int k = 0; k < l->Q; ++k) a.omega[k] = l->omega[k];
+  a.s = l->s;
+  a.dt = l->dt;
+  a.dtR = l->dt * l->R;
+  a.partials = l->red_partials;
+  a.out = l->red_out;
+  LHE_CK(l, launch_reduce(l->p.d, l->p.precision == LHE_FP32_DEV, a, l->red_blocks, l->stream));
+  LHE_CK(l, cudaMemcpyAsync(out_host, l->red_out, sizeof(double) * 4, cudaMemcpyDeviceToHost, l->stream));
+  LHE_CK(l, cudaStreamSynchronize(l->stream));
+  if (out_host[3] > 0.0) return fail(l, LHE_ERR_NONFINITE, "non-finite values in the state");
+  return LHE_OK;
+}
+
+lhe_status lhe_lbm_get_state(lhe_lbm *l, void *buf) {
+  if (lhe_status s = check_handle(l)) return s;
+  if (!buf) return fail(l, LHE_ERR_ARG, "buf is NULL");
+  if (!l->initialised) return fail(l, LHE_ERR_STATE, "no state before lhe_lbm_init");
+  const size_t pb = pop_bytes(l);
+  LHE_CK(l, cudaMemcpyAsync(buf, l->pop[l->cur], pb, cudaMemcpyDefault, l->stream));
+  if (l->p.precision == LHE_FP32_DEV)
+    LHE_CK(l, cudaMemcpyAsync(static_cast<char *>(buf) + pb, l->phi[l->cur], sizeof(double) * (size_t)l->g.S,
+                              cudaMemcpyDefault, l->stream));
+  return LHE_OK;
+}
+
+lhe_status lhe_lbm_set_state(lhe_lbm *l, const void *buf, int64_t step) {
+  if (lhe_status s = check_handle(l)) return s;
+  if (!buf) return fail(l, LHE_ERR_ARG, "buf is NULL");
+  if (step < 0) return fail(l, LHE_ERR_ARG, "step must be >= 0");
+  const size_t pb = pop_bytes(l);
+  LHE_CK(l, cudaMemcpyAsync(l->pop[l->cur], buf, pb, cudaMemcpyDefault, l->stream));
+  if (l->p.precision == LHE_FP32_DEV)
+    LHE_CK(l, cudaMemcpyAsync(l->phi[l->cur], static_cast<const char *>(buf) + pb, sizeof(double) * (size_t)l->g.S,
+                              cudaMemcpyDefault, l->stream));
+  l->step = step;
+  l->initialised = true;
+  return LHE_OK;
+}
+
+lhe_status lhe_lbm_adjoint_seed(lhe_lbm *l, const double *seed) {
+  if (lhe_status s = check_handle(l)) return s;
+  if (!seed) return fail(l, LHE_ERR_ARG, "dL/dphi_T is NULL");
+  if (l->p.bc != LHE_BC_PERIODIC) return fail(l, LHE_ERR_STATE, "the adjoint is implemented for periodic boxes");
+  if (!l->initialised) return fail(l, LHE_ERR_STATE, "lhe_lbm_adjoint_seed before lhe_lbm_init");
+  const bool dev = l->p.precision == LHE_FP32_DEV;
+  const size_t S = (size_t)l->g.S;
+  if (!l->adj[0]) {
+    for (int b = 0; b < 2; ++b) {
+      LHE_CK(l, cudaMalloc(&l->adj[b], pop_bytes(l)));
+      if (dev) LHE_CK(l, cudaMalloc(&l->adjW[b], sizeof(double) * S));
+    }
+    LHE_CK(l, cudaMalloc(&l->gR, sizeof(double) * S));
+  }
+  LHE_CK(l, launch_adjoint_seed(l->p.d, dev, l->g, l->omega, seed, l->adj[0], l->adjW[0], l->gR, l->stream));
+  l->acur = 0;
+  l->adj_ready = true;
+  return LHE_OK;
+}
+
+lhe_status lhe_lbm_adjoint_step(lhe_lbm *l, int64_t n) {
+  if (lhe_status s = check_handle(l)) return s;
+  if (n < 0) return fail(l, LHE_ERR_ARG, "n must be >= 0");
+  if (!l->adj_ready) return fail(l, LHE_ERR_STATE, "lhe_lbm_adjoint_step before lhe_lbm_adjoint_seed");
+  const bool dev = l->p.precision == LHE_FP32_DEV;
+  StepArgs a = step_args(l);
+  a.Rfield = nullptr;
+  a.gR = l->gR;
+  a.nwork = l->g.S;
+  for (int64_t it = 0; it < n; ++it) {
+    a.src = l->adj[l->acur];
+    a.dst = l->adj[1 - l->acur];
+    a.phi_src = l->adjW[l->acur];
+    a.phi_dst = l->adjW[1 - l->acur];
+    cudaError_t e = dev ? launch_step_dev(l->p.d, true, false, a, l->stream)
+                        : launch_step_fp64(l->p.d, true, false, a, l->stream);
+    if (e != cudaSuccess) return cuda_fail(l, e, "adjoint step kernel launch");
+    l->acur ^= 1;
+  }
+  return LHE_OK;
+}
+
+lhe_status lhe_lbm_adjoint_grads(lhe_lbm *l, double *gphi0, double *ggrad, double *gR) {
+  if (lhe_status s = check_handle(l)) return s;
+  if (!l->adj_ready) return fail(l, LHE_ERR_STATE, "lhe_lbm_adjoint_grads before lhe_lbm_adjoint_seed");
+  if (!gphi0) return fail(l, LHE_ERR_ARG, "dL/dphi0 is NULL");
+  const bool dev = l->p.precision == LHE_FP32_DEV;
+  const int d = l->p.d;
+  AdjGradArgs a{};
+  a.g = l->g;
+  a.adj = l->adj[l->acur];
+  a.adjW = l->adjW[l->acur];
+  a.gphi0 = gphi0;
+  a.order = l->init_order_used;
+  double *G = nullptr;
+  if (a.order == 3) {
+    if (l->grad_was_fd) {
+      if (!l->fdgrad) LHE_CK(l, cudaMalloc(&l->fdgrad, sizeof(double) * (size_t)l->g.S * d));
+      G = l->fdgrad;
+    } else {
+      G = ggrad;
+    }
+  }
+  a.G = G;
+  for (int k = 0; k < l->Q; ++k) a.omega[k] = l->omega[k];
+  a.dt = l->dt;
+  a.c = l->p.c;
+  for (int i = 0; i < d; ++i) a.u[i] = l->p.u[i];
+  LHE_CK(l, launch_adjoint_grads(d, dev, a, l->stream));
+  if (a.order == 3 && l->grad_was_fd) LHE_CK(l, launch_fd_grad_transpose_add(d, l->g, l->dx, G, gphi0, l->stream));
+  if (gR) LHE_CK(l, cudaMemcpyAsync(gR, l->gR, sizeof(double) * (size_t)l->g.S, cudaMemcpyDefault, l->stream));
+  return LHE_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,158 @@
+// lhe_internal.h -- host-side handle and kernel launch interfaces of the library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+
+#include "lhe_device.cuh"
+#include "lhe_lbm.h"
+
+namespace lhe {
+
+// Geometry of a box of n_i nodes (x_1 fastest).
+struct Geom {
+  int32_t d = 0;
+  int32_t n[kMaxD] = {1, 1, 1, 1, 1};
+  int32_t stride[kMaxD] = {0, 0, 0, 0, 0};
+  FastDiv dv[kMaxD];   // divide by n_i (site -> coordinates)
+  FastDiv dvi[kMaxD];  // divide by n_i - 2 (interior index -> coordinates)
+  int64_t S = 0;
+  int64_t S_interior = 0;
+};
+
+// Arguments of the fused stream + collide kernels (forward and adjoint, both precisions).
+struct StepArgs {
+  Geom g;
+  const void *src;         // populations at t_n (double or float, Q*S)
+  void *dst;               // populations at t_{n+1}
+  const double *phi_src;   // FP32_DEV: phi at t_n (S)
+  double *phi_dst;         // FP32_DEV: phi at t_{n+1}
+  const double *Rfield;    // per-site source R(x) or nullptr (forward only)
+  double *gR;              // adjoint: dL/dR(x) accumulator (S) or nullptr
+  double omega[kMaxQ];
+  float omega_f[kMaxQ];
+  float dtwR_f[kMaxQ];     // FP32_DEV: dt * omega_k * R (constant source)
+  double s, oms;           // s and 1 - s
+  double dtR;              // dt * R (constant source)
+  double dt;
+  int64_t nwork;           // number of sites processed (S, or the interior count)
+};
+
+// Arguments of the boundary-node kernels (Dirichlet boxes).
+struct BoundaryArgs {
+  Geom g;
+  const int32_t *sites;    // boundary node indices
+  int64_t nsites;
+  const void *src;
+  void *dst;
+  const double *phi_src;
+  double *phi_dst;
+  const double *table;     // per (mode, k): [kc, cos alpha, sin alpha], then ku per mode
+  double omega[kMaxQ];
+  double s, oms, R, dt, dx, c;
+  double x0[kMaxD];        // coordinate of node 0
+  double u[kMaxD];
+  double t_eval;           // time at which the boundary data are evaluated
+  int32_t order;
+  // exact-solution family (lhe_wave)
+  int32_t nmodes;
+  double b;
+  double gl[kMaxD];
+  double a[kMaxModes];
+  double kappa[kMaxModes * kMaxD];
+  double theta[kMaxModes];
+};
+
+struct InitArgs {
+  Geom g;
+  const double *phi0;
+  const double *grad;      // d*S (may be the library's FD buffer)
+  const double *Rfield;
+  void *dst;
+  double *phi_dst;
+  double omega[kMaxQ];
+  double s, oms, dt, dtR, c;
+  double u[kMaxD];
+  int32_t order;
+};
+
+struct ReduceArgs {
+  Geom g;
+  const void *pop;
+  const double *phi;       // FP32_DEV
+  const double *Rfield;
+  double omega[kMaxQ];
+  double s, dt, dtR;
+  double *partials;        // gridDim.x * 4
+  double *out;             // 4 (device)
+};
+
+struct AdjGradArgs {
+  Geom g;
+  const void *adj;         // adjoint populations zeta (FP64) or deviations (FP32_DEV)
+  const double *adjW;      // FP32_DEV: adjoint macroscopic variable W
+  double *gphi0;
+  double *G;               // d*S: (dt/2) sum_k (u - c e_k) zeta_k
+  double omega[kMaxQ];
+  double dt, c;
+  double u[kMaxD];
+  int32_t order;
+};
+
+// Launchers (one per kernel family), implemented in the .cu files; return cudaGetLastError().
+cudaError_t launch_step_fp64(int d, bool adjoint, bool interior, const StepArgs &a, cudaStream_t st);
+cudaError_t launch_step_dev(int d, bool adjoint, bool interior, const StepArgs &a, cudaStream_t st);
+cudaError_t launch_boundary(int d, int kind, bool dev, const BoundaryArgs &a, cudaStream_t st);
+cudaError_t launch_init(int d, bool dev, const InitArgs &a, cudaStream_t st);
+cudaError_t launch_macro_fp64(int d, const StepArgs &a, double *phi_out, cudaStream_t st);
+cudaError_t launch_fd_grad(int d, const Geom &g, double dx, const double *phi, double *grad, cudaStream_t st);
+cudaError_t launch_fd_grad_transpose_add(int d, const Geom &g, double dx, const double *G, double *out,
+                                         cudaStream_t st);
+cudaError_t launch_reduce(int d, bool dev, const ReduceArgs &a, int nblocks, cudaStream_t st);
+cudaError_t launch_adjoint_seed(int d, bool dev, const Geom &g, const double *omega, const double *seed,
+                                void *adj, double *adjW, double *gR, cudaStream_t st);
+cudaError_t launch_adjoint_grads(int d, bool dev, const AdjGradArgs &a, cudaStream_t st);
+
+}  // namespace lhe
+
+// The opaque handle of the C ABI.
+struct lhe_lbm {
+  lhe_lbm_params p{};
+  lhe::Geom g;
+  int Q = 0;
+  double dx = 0, dt = 0, s = 2, R = 0;
+  double omega[lhe::kMaxQ] = {};
+  double m4[10] = {};
+  int32_t e[lhe::kMaxQ * lhe::kMaxD] = {};
+  double x0[lhe::kMaxD] = {};
+  cudaStream_t stream = nullptr;
+  // forward state (ping-pong); FP64: double[Q*S]; FP32_DEV: float[Q*S] + phi double[S]
+  void *pop[2] = {nullptr, nullptr};
+  double *phi[2] = {nullptr, nullptr};
+  int cur = 0;
+  bool initialised = false;
+  int64_t step = 0;
+  double *Rfield = nullptr;     // owned copy of the per-site source, or nullptr
+  bool grad_was_fd = false;
+  int init_order_used = 3;
+  double *fdgrad = nullptr;     // d*S scratch for the finite-difference gradient
+  // Dirichlet
+  int32_t *bsites = nullptr;
+  int64_t nb = 0;
+  bool have_wave = false;
+  lhe_wave wave{};
+  double *bc_table = nullptr;
+  // adjoint
+  void *adj[2] = {nullptr, nullptr};
+  double *adjW[2] = {nullptr, nullptr};
+  double *gR = nullptr;
+  int acur = 0;
+  bool adj_ready = false;
+  // diagnostics
+  double *red_partials = nullptr;
+  double *red_out = nullptr;
+  int red_blocks = 0;
+  std::string err;
+};

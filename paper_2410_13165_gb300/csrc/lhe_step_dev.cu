@@ -1,0 +1,102 @@
+// lhe_step_dev.cu -- fused pull-stream + BGK collision with populations stored as FP32 deviations
+// from the local equilibrium and the macroscopic variable stored and accumulated in FP64.
+//
+// State at t_n: phi(x) (FP64) and g*_k(x) = f*_k(x) - omega_k phi(x) (FP32), f* post-collision.
+// With delta_k = phi(x - e_k) - phi(x) (forward pull direction):
+//   f_k(x)      = omega_k phi(x - e_k) + g*_k(x - e_k)
+//   phi_new(x)  = sum_k f_k(x) = phi(x) + Delta,   Delta = sum_k omega_k delta_k + sum_k g*_k(x - e_k)
+//   g_k         = f_k - omega_k phi_new = omega_k (delta_k - Delta) + g*_k(x - e_k)
+//   g*_k(new)   = (1 - s) g_k + dt omega_k R(x)                 (Eq. (BGK-LB-Evolution))
+// Delta and the deviations are O(dx) and carried in FP32; phi is accumulated in FP64. The
+// neighbour differences delta_k are formed from exact float-pair splits of the FP64 phi values
+// (integer operations only), so no FP64 arithmetic is spent on them.
+//
+// The adjoint uses the same kernel with the reverse pull (x + e_k), no source, and the weighted
+// adjoint variable zeta_k = omega_k W + eps_k (W in FP64, eps in FP32); W_new is accumulated into
+// dL/dR(x) += dt W_new.
+#include "lhe_internal.h"
+#include "lhe_sites.cuh"
+
+namespace lhe {
+
+template <int D, bool ADJ, bool INTERIOR, bool S2>
+__global__ void __launch_bounds__(256) k_step_dev(const StepArgs a) {
+  constexpr Lattice<D> L{};
+  constexpr int Q = Lattice<D>::Q;
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= a.nwork) return;
+  int x[D];
+  const int32_t site = decode_site<D, INTERIOR>(a.g, t, x);
+  int32_t om[D], op[D];
+  axis_offsets<D, INTERIOR>(a.g, x, om, op);
+  const float *__restrict__ src = static_cast<const float *>(a.src);
+  float *__restrict__ dst = static_cast<float *>(a.dst);
+  const double *__restrict__ phis = a.phi_src;
+  const int64_t S = a.g.S;
+
+  const double phi0 = __ldg(phis + site);
+  float h0, l0;
+  split_pair(phi0, h0, l0);
+  float dl[Q], gk[Q];
+  float accw = 0.0f, accg = 0.0f;
+#pragma unroll
+  for (int k = 0; k < Q; ++k) {
+    const int32_t o = source_site<D, ADJ>(L, k, site, om, op);
+    gk[k] = __ldg(src + k * S + o);
+    if (k == 0) {
+      dl[k] = 0.0f;
+    } else {
+      float hk, lk;
+      split_pair(__ldg(phis + o), hk, lk);
+      dl[k] = (hk - h0) + (lk - l0);
+    }
+    accw = fmaf(a.omega_f[k], dl[k], accw);
+    accg += gk[k];
+  }
+  const float Delta = accw + accg;
+  const double phin = phi0 + (double)Delta;
+  a.phi_dst[site] = phin;
+  if (ADJ && a.gR) a.gR[site] = fma(a.dt, phin, a.gR[site]);
+  float dtR = 0.0f;
+  const bool field = !ADJ && a.Rfield != nullptr;
+  if (field) dtR = (float)(a.dt * __ldg(a.Rfield + site));
+  const float oms = (float)a.oms;
+#pragma unroll
+  for (int k = 0; k < Q; ++k) {
+    const float r = fmaf(a.omega_f[k], dl[k] - Delta, gk[k]);  // pre-collision deviation g_k
+    const float src_k = ADJ ? 0.0f : (field ? a.omega_f[k] * dtR : a.dtwR_f[k]);
+    const float out = S2 ? (src_k - r) : fmaf(oms, r, src_k);
+    st_stream(dst + k * S + site, out);
+  }
+}
+
+template <int D, bool ADJ, bool INTERIOR>
+static cudaError_t launch_step_dev_t(const StepArgs &a, cudaStream_t st) {
+  if (a.nwork <= 0) return cudaSuccess;
+  const int threads = 256;
+  const unsigned blocks = (unsigned)((a.nwork + threads - 1) / threads);
+  if (a.s == 2.0)
+    k_step_dev<D, ADJ, INTERIOR, true><<<blocks, threads, 0, st>>>(a);
+  else
+    k_step_dev<D, ADJ, INTERIOR, false><<<blocks, threads, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <int D>
+static cudaError_t step_dev_d(bool adjoint, bool interior, const StepArgs &a, cudaStream_t st) {
+  if (adjoint) return interior ? launch_step_dev_t<D, true, true>(a, st) : launch_step_dev_t<D, true, false>(a, st);
+  return interior ? launch_step_dev_t<D, false, true>(a, st) : launch_step_dev_t<D, false, false>(a, st);
+}
+
+cudaError_t launch_step_dev(int d, bool adjoint, bool interior, const StepArgs &a, cudaStream_t st) {
+  switch (d) {
+    case 1: return step_dev_d<1>(adjoint, interior, a, st);
+    case 2: return step_dev_d<2>(adjoint, interior, a, st);
+    case 3: return step_dev_d<3>(adjoint, interior, a, st);
+    case 4: return step_dev_d<4>(adjoint, interior, a, st);
+    case 5: return step_dev_d<5>(adjoint, interior, a, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace lhe

@@ -1,0 +1,106 @@
+// lhe_step_fp64.cu -- fused pull-stream + BGK collision on DdQ(2d^2+1), FP64 populations.
+//
+// Forward (Eq. (BGK-LB-Evolution)), stored state = post-collision populations f*:
+//   f_k(x)  = f*_k(x - e_k)                      (pull; periodic wrap or interior of a Dirichlet box)
+//   phi(x)  = sum_k f_k(x)                       (Eq. (0-1-meq))
+//   f*_k(x) = (1 - s) f_k + omega_k (s phi + dt R(x))      (s = 2: omega_k (2 phi + dt R) - f_k)
+// Adjoint (transpose of the step, in the weighted variable zeta_k = omega_k nu_k):
+//   mu_k(x) = zeta_k(x + e_k)                    (reverse pull)
+//   w(x)    = sum_k mu_k(x),  gR(x) += dt w(x)
+//   zeta_k  = (1 - s) mu_k + omega_k s w
+// Both are one thread per site, x_1 fastest, SoA population arrays pop[k*S + site].
+#include "lhe_internal.h"
+#include "lhe_sites.cuh"
+
+namespace lhe {
+
+template <int D, bool ADJ, bool INTERIOR, bool S2>
+__global__ void __launch_bounds__(256) k_step_fp64(const StepArgs a) {
+  constexpr Lattice<D> L{};
+  constexpr int Q = Lattice<D>::Q;
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= a.nwork) return;
+  int x[D];
+  const int32_t site = decode_site<D, INTERIOR>(a.g, t, x);
+  int32_t om[D], op[D];
+  axis_offsets<D, INTERIOR>(a.g, x, om, op);
+  const double *__restrict__ src = static_cast<const double *>(a.src);
+  double *__restrict__ dst = static_cast<double *>(a.dst);
+  const int64_t S = a.g.S;
+  double f[Q];
+#pragma unroll
+  for (int k = 0; k < Q; ++k) f[k] = __ldg(src + k * S + source_site<D, ADJ>(L, k, site, om, op));
+  double psi;
+  if (ADJ) {
+    const double w = fixed_moment_sum<Q>(f, 1.0, 0.0);
+    psi = (S2 ? 2.0 : a.s) * w;
+    if (a.gR) a.gR[site] = fma(a.dt, w, a.gR[site]);
+  } else {
+    const double add = a.Rfield ? a.dt * __ldg(a.Rfield + site) : a.dtR;
+    psi = fixed_moment_sum<Q>(f, S2 ? 2.0 : a.s, add);
+  }
+#pragma unroll
+  for (int k = 0; k < Q; ++k) {
+    const double out = S2 ? fma(a.omega[k], psi, -f[k]) : fma(a.omega[k], psi, a.oms * f[k]);
+    st_stream(dst + k * S + site, out);
+  }
+}
+
+template <int D>
+__global__ void __launch_bounds__(256) k_macro_fp64(const StepArgs a, double *__restrict__ phi) {
+  constexpr int Q = Lattice<D>::Q;
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= a.g.S) return;
+  const double *__restrict__ src = static_cast<const double *>(a.src);
+  double f[Q];
+#pragma unroll
+  for (int k = 0; k < Q; ++k) f[k] = src[k * a.g.S + t];
+  const double dtR = a.Rfield ? a.dt * a.Rfield[t] : a.dtR;
+  // phi(t_n) = sum_k f*_k(x, t_n) - dt R(x): the collision keeps sum_k f_k and adds dt R.
+  phi[t] = fixed_moment_sum<Q>(f, 1.0, -dtR);
+}
+
+template <int D, bool ADJ, bool INTERIOR>
+static cudaError_t launch_step_fp64_t(const StepArgs &a, cudaStream_t st) {
+  if (a.nwork <= 0) return cudaSuccess;
+  const int threads = 256;
+  const unsigned blocks = (unsigned)((a.nwork + threads - 1) / threads);
+  if (a.s == 2.0)
+    k_step_fp64<D, ADJ, INTERIOR, true><<<blocks, threads, 0, st>>>(a);
+  else
+    k_step_fp64<D, ADJ, INTERIOR, false><<<blocks, threads, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <int D>
+static cudaError_t step_fp64_d(bool adjoint, bool interior, const StepArgs &a, cudaStream_t st) {
+  if (adjoint) return interior ? launch_step_fp64_t<D, true, true>(a, st) : launch_step_fp64_t<D, true, false>(a, st);
+  return interior ? launch_step_fp64_t<D, false, true>(a, st) : launch_step_fp64_t<D, false, false>(a, st);
+}
+
+cudaError_t launch_step_fp64(int d, bool adjoint, bool interior, const StepArgs &a, cudaStream_t st) {
+  switch (d) {
+    case 1: return step_fp64_d<1>(adjoint, interior, a, st);
+    case 2: return step_fp64_d<2>(adjoint, interior, a, st);
+    case 3: return step_fp64_d<3>(adjoint, interior, a, st);
+    case 4: return step_fp64_d<4>(adjoint, interior, a, st);
+    case 5: return step_fp64_d<5>(adjoint, interior, a, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_macro_fp64(int d, const StepArgs &a, double *phi_out, cudaStream_t st) {
+  const int threads = 256;
+  const unsigned blocks = (unsigned)((a.g.S + threads - 1) / threads);
+  switch (d) {
+    case 1: k_macro_fp64<1><<<blocks, threads, 0, st>>>(a, phi_out); break;
+    case 2: k_macro_fp64<2><<<blocks, threads, 0, st>>>(a, phi_out); break;
+    case 3: k_macro_fp64<3><<<blocks, threads, 0, st>>>(a, phi_out); break;
+    case 4: k_macro_fp64<4><<<blocks, threads, 0, st>>>(a, phi_out); break;
+    case 5: k_macro_fp64<5><<<blocks, threads, 0, st>>>(a, phi_out); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace lhe

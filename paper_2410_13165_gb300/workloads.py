@@ -1,0 +1,106 @@
+"""Seeded synthetic inputs shared by the CUDA path's tests and benchmark and by the oracle's tests.
+
+This module holds none of the method's arithmetic: it draws workload parameters from a
+counter-based generator and evaluates smooth input fields (initial data, their gradients, target
+and source fields) on the lattice nodes. Numbers come from splitmix64 (Steele, Lea & Flood,
+"Fast splittable pseudorandom number generators", OOPSLA 2014), so they are identical on every
+machine.
+
+Workload recipe (the paper's data are analytic, Example 2/3): phi0(x) = sum_m a_m sin(kappa_m .
+(x - lo) + theta_m) with kappa_m = 2 pi k_m / L, k_m in {1..kmax}^d (independent uniform integer
+components), a_m ~ U(-1, 1), theta_m ~ U(0, 2 pi). The exact solution of the L-HE with constant
+R is phi0(x - u t) + R t.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+_MASK = (1 << 64) - 1
+
+
+class SplitMix64:
+    def __init__(self, seed: int):
+        self.state = seed & _MASK
+
+    def next_u64(self) -> int:
+        self.state = (self.state + 0x9E3779B97F4A7C15) & _MASK
+        z = self.state
+        z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & _MASK
+        z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & _MASK
+        return z ^ (z >> 31)
+
+    def uniform(self, lo: float = 0.0, hi: float = 1.0) -> float:
+        return lo + (hi - lo) * ((self.next_u64() >> 11) * (1.0 / (1 << 53)))
+
+    def integer(self, lo: int, hi: int) -> int:
+        """Uniform integer in [lo, hi]."""
+        return lo + self.next_u64() % (hi - lo + 1)
+
+
+SEED_BASE = 2410131650
+
+
+class FourierField:
+    """phi(x) = sum_m a_m sin(kappa_m . (x - lo) + theta_m) on a box with lower corner lo."""
+
+    def __init__(self, a, k, theta, L, lo):
+        self.a = np.asarray(a, dtype=np.float64)
+        self.k = np.asarray(k, dtype=np.int64)
+        self.theta = np.asarray(theta, dtype=np.float64)
+        self.L = np.asarray(L, dtype=np.float64)
+        self.lo = np.asarray(lo, dtype=np.float64)
+        self.kappa = 2.0 * np.pi * self.k / self.L[None, :]
+
+    @property
+    def d(self):
+        return self.k.shape[1]
+
+    def value(self, X: np.ndarray, shift=None) -> np.ndarray:
+        """X: (d, S) coordinates; shift: optional displacement subtracted from X (e.g. u t)."""
+        Y = X - self.lo[:, None] - (0.0 if shift is None else np.asarray(shift, dtype=np.float64)[:, None])
+        return np.sum(self.a[:, None] * np.sin(self.kappa @ Y + self.theta[:, None]), axis=0)
+
+    def grad(self, X: np.ndarray, shift=None) -> np.ndarray:
+        Y = X - self.lo[:, None] - (0.0 if shift is None else np.asarray(shift, dtype=np.float64)[:, None])
+        c = self.a[:, None] * np.cos(self.kappa @ Y + self.theta[:, None])  # (M, S)
+        return self.kappa.T @ c                                             # (d, S)
+
+    def wave_params(self):
+        """The same field written as sum_m a_m sin(kappa_m . x + theta'_m) (absolute coordinates)."""
+        theta_abs = self.theta - self.kappa @ self.lo
+        return list(self.a), [list(r) for r in self.kappa], list(theta_abs)
+
+
+def fourier_field(d: int, nmodes: int, seed: int, lo=0.0, hi=1.0, kmax: int = 3) -> FourierField:
+    rng = SplitMix64(SEED_BASE + seed)
+    lo = np.broadcast_to(np.asarray(lo, dtype=np.float64), (d,))
+    hi = np.broadcast_to(np.asarray(hi, dtype=np.float64), (d,))
+    a, k, th = [], [], []
+    for _ in range(nmodes):
+        a.append(rng.uniform(-1.0, 1.0))
+        k.append([rng.integer(1, kmax) for _ in range(d)])
+        th.append(rng.uniform(0.0, 2.0 * math.pi))
+    return FourierField(a, k, th, hi - lo, lo)
+
+
+def node_coords(d: int, n, lo, dx: float, halfway: bool = False) -> np.ndarray:
+    """(d, S) node coordinates, x_1 fastest: lo + i dx (periodic, full-way) or lo + (i + 1/2) dx."""
+    n = list(n) if hasattr(n, "__len__") else [n] * d
+    lo = np.broadcast_to(np.asarray(lo, dtype=np.float64), (d,))
+    axes = [lo[i] + dx * (np.arange(n[i]) + (0.5 if halfway else 0.0)) for i in range(d)]
+    grids = np.meshgrid(*axes[::-1], indexing="ij")[::-1]
+    return np.stack([g.ravel() for g in grids])
+
+
+def lattice_spacing(n: int, lo: float, hi: float, bc: str) -> float:
+    return (hi - lo) / ((n - 1) if bc == "fullway" else n)
+
+
+def periodic_problem(d: int, n: int, nmodes: int, seed: int, lo=0.0, hi=1.0):
+    """phi0, grad phi0 (numpy) and the field of a periodic Fourier workload on n^d nodes."""
+    dx = (hi - lo) / n
+    X = node_coords(d, n, lo, dx)
+    F = fourier_field(d, nmodes, seed, lo, hi)
+    return F.value(X), F.grad(X), F, X

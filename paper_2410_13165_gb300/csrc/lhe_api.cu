@@ -184,6 +184,7 @@ StepArgs step_args(const lhe_lbm *l) {
   a.oms = 1.0 - l->s;
   a.dtR = l->dt * l->R;
   a.dt = l->dt;
+  a.half_dt = 0.5 * l->dt;
   a.Rfield = l->Rfield;
   return a;
 }
@@ -271,7 +272,7 @@ lhe_status lhe_lbm_create(const lhe_lbm_params *p, lhe_lbm **out) {
     cudaError_t e = cudaMalloc(&l->pop[b], pb);
     if (e != cudaSuccess) return bail(cuda_fail(l, e, "cudaMalloc(populations)"));
     if (p->precision == LHE_FP32_DEV) {
-      e = cudaMalloc(&l->phi[b], sizeof(double) * (size_t)S);
+      e = cudaMalloc(&l->phi[b], sizeof(float2) * (size_t)S);
       if (e != cudaSuccess) return bail(cuda_fail(l, e, "cudaMalloc(phi)"));
     }
   }
@@ -339,7 +340,7 @@ lhe_status lhe_lbm_info(const lhe_lbm *l, lhe_lbm_info_t *info) {
   std::memcpy(info->m4, l->m4, sizeof(l->m4));
   std::memcpy(info->omega, l->omega, sizeof(double) * l->Q);
   std::memcpy(info->e, l->e, sizeof(int32_t) * l->Q * l->p.d);
-  info->state_bytes = pop_bytes(l) + (l->p.precision == LHE_FP32_DEV ? sizeof(double) * (size_t)l->g.S : 0);
+  info->state_bytes = pop_bytes(l) + (l->p.precision == LHE_FP32_DEV ? sizeof(float2) * (size_t)l->g.S : 0);
   return LHE_OK;
 }
 
@@ -493,7 +494,7 @@ lhe_status lhe_lbm_macro(lhe_lbm *l, double *phi_out) {
   if (!phi_out) return fail(l, LHE_ERR_ARG, "phi_out is NULL");
   if (!l->initialised) return fail(l, LHE_ERR_STATE, "lhe_lbm_macro before lhe_lbm_init");
   if (l->p.precision == LHE_FP32_DEV) {
-    LHE_CK(l, cudaMemcpyAsync(phi_out, l->phi[l->cur], sizeof(double) * (size_t)l->g.S, cudaMemcpyDefault, l->stream));
+    LHE_CK(l, launch_df_to_double(l->phi[l->cur], phi_out, l->g.S, l->stream));
     return LHE_OK;
   }
   StepArgs a = step_args(l);
@@ -531,7 +532,7 @@ lhe_status lhe_lbm_get_state(lhe_lbm *l, void *buf) {
   const size_t pb = pop_bytes(l);
   LHE_CK(l, cudaMemcpyAsync(buf, l->pop[l->cur], pb, cudaMemcpyDefault, l->stream));
   if (l->p.precision == LHE_FP32_DEV)
-    LHE_CK(l, cudaMemcpyAsync(static_cast<char *>(buf) + pb, l->phi[l->cur], sizeof(double) * (size_t)l->g.S,
+    LHE_CK(l, cudaMemcpyAsync(static_cast<char *>(buf) + pb, l->phi[l->cur], sizeof(float2) * (size_t)l->g.S,
                               cudaMemcpyDefault, l->stream));
   return LHE_OK;
 }
@@ -543,7 +544,7 @@ lhe_status lhe_lbm_set_state(lhe_lbm *l, const void *buf, int64_t step) {
   const size_t pb = pop_bytes(l);
   LHE_CK(l, cudaMemcpyAsync(l->pop[l->cur], buf, pb, cudaMemcpyDefault, l->stream));
   if (l->p.precision == LHE_FP32_DEV)
-    LHE_CK(l, cudaMemcpyAsync(l->phi[l->cur], static_cast<const char *>(buf) + pb, sizeof(double) * (size_t)l->g.S,
+    LHE_CK(l, cudaMemcpyAsync(l->phi[l->cur], static_cast<const char *>(buf) + pb, sizeof(float2) * (size_t)l->g.S,
                               cudaMemcpyDefault, l->stream));
   l->step = step;
   l->initialised = true;
@@ -560,7 +561,7 @@ lhe_status lhe_lbm_adjoint_seed(lhe_lbm *l, const double *seed) {
   if (!l->adj[0]) {
     for (int b = 0; b < 2; ++b) {
       LHE_CK(l, cudaMalloc(&l->adj[b], pop_bytes(l)));
-      if (dev) LHE_CK(l, cudaMalloc(&l->adjW[b], sizeof(double) * S));
+      if (dev) LHE_CK(l, cudaMalloc(&l->adjW[b], sizeof(float2) * S));
     }
     LHE_CK(l, cudaMalloc(&l->gR, sizeof(double) * S));
   }

@@ -79,7 +79,7 @@ __global__ void __launch_bounds__(128) k_boundary(const BoundaryArgs a) {
       }
     }
     if (inside) {
-      v[k] = DEV ? fma(a.omega[k], a.phi_src[o], (double)gsrc[k * S + o]) : fsrc[k * S + o];
+      v[k] = DEV ? fma(a.omega[k], df_value(a.phi_src[o]), (double)gsrc[k * S + o]) : fsrc[k * S + o];
       continue;
     }
     double gc = 0.0;  // g . c_k
@@ -128,7 +128,8 @@ __global__ void __launch_bounds__(128) k_boundary(const BoundaryArgs a) {
       if (a.order >= 2) Bk += 0.5 * dt * wp * D01 + 0.5 * dt * wp * a.R;
       if (a.order >= 3) Bk += -dt2 / 8.0 * wp * D20 - dt2 / 4.0 * wm * D11;
       if (a.order >= 4) Bk += -dt3 / 8.0 * wm * D12 - dt3 / 16.0 * wp * D21 - dt3 / 24.0 * wp * D03;
-      const double fkb = DEV ? fma(a.omega[kb], a.phi_src[site], (double)gsrc[kb * S + site]) : fsrc[kb * S + site];
+      const double fkb = DEV ? fma(a.omega[kb], df_value(a.phi_src[site]), (double)gsrc[kb * S + site])
+                              : fsrc[kb * S + site];
       v[k] = Bk - fkb;
     }
   }
@@ -143,7 +144,7 @@ __global__ void __launch_bounds__(128) k_boundary(const BoundaryArgs a) {
       const double fs = fma(a.omega[k], psi, a.oms * v[k]);
       gdst[k * S + site] = (float)(fs - a.omega[k] * phi);
     }
-    a.phi_dst[site] = phi;
+    a.phi_dst[site] = df_split(phi);
   } else {
     double *fdst = static_cast<double *>(a.dst);
 #pragma unroll

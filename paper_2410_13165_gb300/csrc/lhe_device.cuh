@@ -12,6 +12,11 @@ constexpr int kMaxD = 5;
 constexpr int kMaxQ = 51;
 constexpr int kMaxModes = 16;
 
+// Threads per block of the fused step kernels (one thread per lattice node).
+#ifndef LHE_STEP_THREADS
+#define LHE_STEP_THREADS 128
+#endif
+
 // ----------------------------------------------------------------------------------------------
 // Lattice (Sec. 2.3, Eq. (DdQ-M)): k = 0 rest; k = 1..d: +e_i; k = d+1..2d: -e_i; then for each
 // pair i<j (lexicographic) four velocities with component i from J1 = (1,-1,-1,1) and component
@@ -84,69 +89,70 @@ __host__ __device__ constexpr int ceil_log2(int q) {
   return l;
 }
 
-// Moment sum sum_k f_k of Q doubles accumulated exactly in 64-bit fixed point, aligned to the
-// largest exponent: each term's 53-bit significand is shifted into a common frame with G guard
-// bits (G = 10 - ceil(log2 Q) keeps Q terms below 2^63) and rounded to nearest on the way. The
-// result is mult * sum + add with one rounding of the integer total. The error is below one
-// unit in the last place of the largest |f_k| (sequential FP64 addition: up to (Q-1)/2 units).
-// GB300 executes FP64 arithmetic and FP32<->FP64 conversions at ~2 per clock per SM, integer
-// arithmetic ~30x faster; this moves the Q-1 additions of the moment sum off the FP64 pipe.
-// NaN or Inf inputs fall back to plain FP64 addition so they propagate.
-template <int Q>
-__device__ __forceinline__ double fixed_moment_sum(const double (&f)[Q], double mult, double add) {
+// Moment sum of Q doubles, accumulated exactly in 64-bit fixed point on the integer pipes.
+// Each term's 53-bit significand is placed, with G guard bits (G = 10 - ceil(log2 Q) keeps Q terms
+// below 2^63), in the frame of the largest exponent present, rounding to nearest (ties up) when it
+// is shifted right; the integer total is converted back to a correctly rounded double (ties to even)
+// with integer operations only, times 2^P2. The error is below one unit in the last place of the
+// largest |f_k| (sequential FP64 addition: up to (Q-1)/2 units). GB300 runs FP64 arithmetic and
+// FP32<->FP64 conversions at ~2 per clock per SM and integer arithmetic far faster, so this takes
+// the Q-1 additions of the moment sum (and the conversion) off the FP64 pipe.
+// Subnormal terms are placed as if their exponent were 0 instead of 1 (an error below 2^-1022 in
+// absolute value); any NaN or infinite term makes the result NaN.
+template <int Q, int P2>
+__device__ __forceinline__ double fixed_moment_sum(const double (&f)[Q]) {
   constexpr int G = 10 - ceil_log2(Q);
   static_assert(G >= 3, "too many terms for a 64-bit accumulator");
-  int emax = 0;
+  unsigned emf = 0u;  // largest exponent field, in place (bits 20..30 of the high word)
 #pragma unroll
-  for (int k = 0; k < Q; ++k) emax = max(emax, (__double2hiint(f[k]) >> 20) & 0x7FF);
-  if (emax == 0x7FF) {
-    double s = 0.0;
-#pragma unroll
-    for (int k = 0; k < Q; ++k) s += f[k];
-    return fma(mult, s, add);
-  }
-  const int E = max(emax, 1);
+  for (int k = 0; k < Q; ++k) emf = max(emf, (unsigned)__double2hiint(f[k]) & 0x7FF00000u);
+  if (emf == 0x7FF00000u) return __longlong_as_double(0x7FF8000000000000ll);
+  emf = max(emf, 0x00100000u);
   long long acc = 0;
 #pragma unroll
   for (int k = 0; k < Q; ++k) {
     const unsigned hi = (unsigned)__double2hiint(f[k]);
     const unsigned lo = (unsigned)__double2loint(f[k]);
-    const int e = (int)((hi >> 20) & 0x7FFu);
-    const unsigned mh = (hi & 0xFFFFFu) | (e ? 0x100000u : 0u);
-    const unsigned long long mg = ((((unsigned long long)mh) << 32) | lo) << G;  // < 2^(53+G)
-    const int sh = E - max(e, 1);
+    const unsigned ef = hi & 0x7FF00000u;
+    const unsigned mh = (hi & 0x000FFFFFu) | min(ef, 0x00100000u);  // implicit bit unless zero/subnormal
+    const unsigned sh = (emf - max(ef, 0x00100000u)) >> 20;
+    const unsigned long long m = ((((unsigned long long)mh) << 32) | lo) << G;  // < 2^(53+G)
     unsigned long long v;
-    if (sh == 0) v = mg;
-    else if (sh <= 53 + G) v = (mg + (1ull << (sh - 1))) >> sh;  // round half up
+    if (sh < 32u) v = (m + ((1ull << sh) >> 1)) >> sh;
+    else if (sh < 64u) v = (m + (1ull << (sh - 1))) >> sh;
     else v = 0ull;
-    acc += (hi >> 31) ? -(long long)v : (long long)v;
+    const long long sg = (long long)((int)hi >> 31);  // 0 or -1
+    acc += ((long long)v ^ sg) - sg;
   }
-  const double a = __ll2double_rn(acc);
-  const int p = E - 1075 - G;
-  if (p >= -1022) return fma(a, mult * pow2_bits(p), add);
-  return fma(a * pow2_bits(p + 600), mult * pow2_bits(-600), add);
+  if (acc == 0) return 0.0;
+  const unsigned long long sbit = acc < 0 ? 0x8000000000000000ull : 0ull;
+  unsigned long long a = acc < 0 ? (unsigned long long)(-acc) : (unsigned long long)acc;
+  const int lz = __clzll((long long)a);
+  a <<= lz;                                  // leading one at bit 63
+  unsigned long long mant = a >> 11;         // 53 bits with the leading one
+  const unsigned rem = (unsigned)a & 0x7FFu; // dropped bits
+  mant += (rem > 0x400u || (rem == 0x400u && (mant & 1ull))) ? 1ull : 0ull;
+  int ex = (63 - lz) + (int)(emf >> 20) - 1075 - G + 1023 + P2;
+  if (mant >> 53) {
+    mant >>= 1;
+    ++ex;
+  }
+  if (ex <= 0 || ex >= 2047) {  // result outside the normal range: convert and scale in two exact steps
+    const int p = (int)(emf >> 20) - 1075 - G + P2;
+    const int p1 = p / 2;
+    return __ll2double_rn(acc) * pow2_bits(p1) * pow2_bits(p - p1);
+  }
+  return __longlong_as_double((long long)(sbit | ((unsigned long long)ex << 52) | (mant & 0xFFFFFFFFFFFFFull)));
 }
 
-// Split a double into an unevaluated float pair x ~ h + l without FP64 arithmetic: h is x with
-// its significand truncated to 24 bits, l the next 23 bits of the residual (|x - h - l| < 2^-47 |x|).
-// Values outside the normal float range take the (rare) FP64 conversion path.
-__device__ __forceinline__ void split_pair(double x, float &h, float &l) {
-  const unsigned hi = (unsigned)__double2hiint(x);
-  const unsigned lo = (unsigned)__double2loint(x);
-  const int e = (int)((hi >> 20) & 0x7FFu);
-  const int ef = e - 896;  // float biased exponent of the leading part
-  if (ef >= 1 && ef <= 254) {
-    const unsigned sign = hi & 0x80000000u;
-    h = __uint_as_float(sign | ((unsigned)ef << 23) | ((hi & 0xFFFFFu) << 3) | (lo >> 29));
-    const unsigned r23 = (lo & 0x1FFFFFFFu) >> 6;
-    const float rf = __uint_as_float(0x4B000000u | r23) - 8388608.0f;  // exact: r23 < 2^23
-    const int es = e - 942;                                              // 2^(e - 1075 + 6)
-    const float lv = (es >= 1) ? rf * __uint_as_float((unsigned)es << 23) : 0.0f;
-    l = __uint_as_float(__float_as_uint(lv) ^ sign);
-  } else {
-    h = __double2float_rn(x);
-    l = 0.0f;
-  }
+// Double-float storage of the macroscopic variable of the FP32-deviation form: phi = h + l with h
+// the value truncated to 24 significant bits and l the rounded residual (a 48-bit significand,
+// relative spacing 2^-48). Neighbour differences are then plain FP32 arithmetic.
+__device__ __forceinline__ double df_value(float2 p) { return (double)p.x + (double)p.y; }
+
+__device__ __forceinline__ float2 df_split(double x) {
+  const double hd = __hiloint2double(__double2hiint(x), __double2loint(x) & (int)0xE0000000);
+  return make_float2((float)hd, (float)(x - hd));
 }
 
 // Streaming stores: the new state is not re-read by this kernel.

@@ -27,8 +27,8 @@ struct StepArgs {
   Geom g;
   const void *src;         // populations at t_n (double or float, Q*S)
   void *dst;               // populations at t_{n+1}
-  const double *phi_src;   // FP32_DEV: phi at t_n (S)
-  double *phi_dst;         // FP32_DEV: phi at t_{n+1}
+  const float2 *phi_src;   // FP32_DEV: phi at t_n as a double-float pair (S)
+  float2 *phi_dst;         // FP32_DEV: phi at t_{n+1}
   const double *Rfield;    // per-site source R(x) or nullptr (forward only)
   double *gR;              // adjoint: dL/dR(x) accumulator (S) or nullptr
   double omega[kMaxQ];
@@ -36,7 +36,7 @@ struct StepArgs {
   float dtwR_f[kMaxQ];     // FP32_DEV: dt * omega_k * R (constant source)
   double s, oms;           // s and 1 - s
   double dtR;              // dt * R (constant source)
-  double dt;
+  double dt, half_dt;
   int64_t nwork;           // number of sites processed (S, or the interior count)
 };
 
@@ -47,8 +47,8 @@ struct BoundaryArgs {
   int64_t nsites;
   const void *src;
   void *dst;
-  const double *phi_src;
-  double *phi_dst;
+  const float2 *phi_src;
+  float2 *phi_dst;
   const double *table;     // per (mode, k): [kc, cos alpha, sin alpha], then ku per mode
   double omega[kMaxQ];
   double s, oms, R, dt, dx, c;
@@ -71,7 +71,7 @@ struct InitArgs {
   const double *grad;      // d*S (may be the library's FD buffer)
   const double *Rfield;
   void *dst;
-  double *phi_dst;
+  float2 *phi_dst;
   double omega[kMaxQ];
   double s, oms, dt, dtR, c;
   double u[kMaxD];
@@ -81,7 +81,7 @@ struct InitArgs {
 struct ReduceArgs {
   Geom g;
   const void *pop;
-  const double *phi;       // FP32_DEV
+  const float2 *phi;       // FP32_DEV
   const double *Rfield;
   double omega[kMaxQ];
   double s, dt, dtR;
@@ -92,7 +92,7 @@ struct ReduceArgs {
 struct AdjGradArgs {
   Geom g;
   const void *adj;         // adjoint populations zeta (FP64) or deviations (FP32_DEV)
-  const double *adjW;      // FP32_DEV: adjoint macroscopic variable W
+  const float2 *adjW;      // FP32_DEV: adjoint macroscopic variable W
   double *gphi0;
   double *G;               // d*S: (dt/2) sum_k (u - c e_k) zeta_k
   double omega[kMaxQ];
@@ -112,7 +112,8 @@ cudaError_t launch_fd_grad_transpose_add(int d, const Geom &g, double dx, const 
                                          cudaStream_t st);
 cudaError_t launch_reduce(int d, bool dev, const ReduceArgs &a, int nblocks, cudaStream_t st);
 cudaError_t launch_adjoint_seed(int d, bool dev, const Geom &g, const double *omega, const double *seed,
-                                void *adj, double *adjW, double *gR, cudaStream_t st);
+                                void *adj, float2 *adjW, double *gR, cudaStream_t st);
+cudaError_t launch_df_to_double(const float2 *src, double *dst, int64_t n, cudaStream_t st);
 cudaError_t launch_adjoint_grads(int d, bool dev, const AdjGradArgs &a, cudaStream_t st);
 
 }  // namespace lhe
@@ -128,9 +129,9 @@ struct lhe_lbm {
   int32_t e[lhe::kMaxQ * lhe::kMaxD] = {};
   double x0[lhe::kMaxD] = {};
   cudaStream_t stream = nullptr;
-  // forward state (ping-pong); FP64: double[Q*S]; FP32_DEV: float[Q*S] + phi double[S]
+  // forward state (ping-pong); FP64: double[Q*S]; FP32_DEV: float[Q*S] + phi float2[S]
   void *pop[2] = {nullptr, nullptr};
-  double *phi[2] = {nullptr, nullptr};
+  float2 *phi[2] = {nullptr, nullptr};  // FP32_DEV: phi as a double-float pair
   int cur = 0;
   bool initialised = false;
   int64_t step = 0;
@@ -146,7 +147,7 @@ struct lhe_lbm {
   double *bc_table = nullptr;
   // adjoint
   void *adj[2] = {nullptr, nullptr};
-  double *adjW[2] = {nullptr, nullptr};
+  float2 *adjW[2] = {nullptr, nullptr};
   double *gR = nullptr;
   int acur = 0;
   bool adj_ready = false;

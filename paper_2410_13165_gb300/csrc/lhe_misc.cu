@@ -35,7 +35,7 @@ __global__ void __launch_bounds__(256) k_init(const InitArgs a) {
       static_cast<double *>(a.dst)[k * S + site] = fma(a.omega[k], fma(a.s, phi0, dtR), a.oms * fk);
     }
   }
-  if (DEV) a.phi_dst[site] = phi0;
+  if (DEV) a.phi_dst[site] = df_split(phi0);
 }
 
 template <int D>
@@ -158,7 +158,7 @@ __global__ void __launch_bounds__(256) k_reduce_partials(const ReduceArgs a) {
     double phi, ent = 0.0, bad = 0.0;
     if (DEV) {
       const float *g = static_cast<const float *>(a.pop);
-      phi = a.phi[site];
+      phi = df_value(a.phi[site]);
       if (!isfinite(phi)) bad += 1.0;
       ent = 0.5 * phi * phi;  // sum_k f_k^2/(2 w_k) = phi^2/2 + sum_k g_k^2/(2 w_k) since sum_k g_k = 0
       for (int k = 0; k < Q; ++k) {
@@ -229,7 +229,7 @@ cudaError_t launch_reduce(int d, bool dev, const ReduceArgs &a, int nblocks, cud
 // zeta_k = omega_k nu_k (FP64) or as W = dL/dphi_T, eps_k = 0 (FP32_DEV); dL/dR := 0.
 template <int D, bool DEV>
 __global__ void __launch_bounds__(256) k_adj_seed(const Geom g, const StepArgs w, const double *__restrict__ seed,
-                                                  void *adj, double *adjW, double *gR) {
+                                                  void *adj, float2 *adjW, double *gR) {
   constexpr int Q = Lattice<D>::Q;
   const int64_t site = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (site >= g.S) return;
@@ -239,12 +239,12 @@ __global__ void __launch_bounds__(256) k_adj_seed(const Geom g, const StepArgs w
     if (DEV) static_cast<float *>(adj)[k * g.S + site] = 0.0f;
     else static_cast<double *>(adj)[k * g.S + site] = w.omega[k] * s0;
   }
-  if (DEV) adjW[site] = s0;
+  if (DEV) adjW[site] = df_split(s0);
   gR[site] = 0.0;
 }
 
 template <int D>
-static cudaError_t seed_d(bool dev, const Geom &g, const StepArgs &w, const double *seed, void *adj, double *adjW,
+static cudaError_t seed_d(bool dev, const Geom &g, const StepArgs &w, const double *seed, void *adj, float2 *adjW,
                           double *gR, cudaStream_t st) {
   const unsigned blocks = (unsigned)((g.S + 255) / 256);
   if (dev) k_adj_seed<D, true><<<blocks, 256, 0, st>>>(g, w, seed, adj, adjW, gR);
@@ -253,7 +253,7 @@ static cudaError_t seed_d(bool dev, const Geom &g, const StepArgs &w, const doub
 }
 
 cudaError_t launch_adjoint_seed(int d, bool dev, const Geom &g, const double *omega, const double *seed, void *adj,
-                                double *adjW, double *gR, cudaStream_t st) {
+                                float2 *adjW, double *gR, cudaStream_t st) {
   StepArgs w{};
   for (int k = 0; k < kMaxQ; ++k) w.omega[k] = omega[k];
   switch (d) {
@@ -277,7 +277,7 @@ __global__ void __launch_bounds__(256) k_adj_grads(const AdjGradArgs a) {
   const int64_t site = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t S = a.g.S;
   if (site >= S) return;
-  double zsum = DEV ? a.adjW[site] : 0.0;
+  double zsum = DEV ? df_value(a.adjW[site]) : 0.0;
   double G[D];
 #pragma unroll
   for (int i = 0; i < D; ++i) G[i] = 0.0;
@@ -312,6 +312,18 @@ cudaError_t launch_adjoint_grads(int d, bool dev, const AdjGradArgs &a, cudaStre
     case 5: return grads_d<5>(dev, a, st);
     default: return cudaErrorInvalidValue;
   }
+}
+
+// phi of the FP32-deviation form: double-float pair -> double.
+__global__ void __launch_bounds__(256) k_df_to_double(const float2 *__restrict__ src, double *__restrict__ dst, int64_t n) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = df_value(src[i]);
+}
+
+cudaError_t launch_df_to_double(const float2 *src, double *dst, int64_t n, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_df_to_double<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(src, dst, n);
+  return cudaGetLastError();
 }
 
 }  // namespace lhe

@@ -1,26 +1,27 @@
 // lhe_step_dev.cu -- fused pull-stream + BGK collision with populations stored as FP32 deviations
-// from the local equilibrium and the macroscopic variable stored and accumulated in FP64.
+// from the local equilibrium and the macroscopic variable accumulated in FP64.
 //
-// State at t_n: phi(x) (FP64) and g*_k(x) = f*_k(x) - omega_k phi(x) (FP32), f* post-collision.
+// State at t_n: phi(x) and g*_k(x) = f*_k(x) - omega_k phi(x) (FP32), f* post-collision; phi is
+// stored as an exact double-float pair h + l (48-bit significand, 8 bytes).
 // With delta_k = phi(x - e_k) - phi(x) (forward pull direction):
 //   f_k(x)      = omega_k phi(x - e_k) + g*_k(x - e_k)
 //   phi_new(x)  = sum_k f_k(x) = phi(x) + Delta,   Delta = sum_k omega_k delta_k + sum_k g*_k(x - e_k)
 //   g_k         = f_k - omega_k phi_new = omega_k (delta_k - Delta) + g*_k(x - e_k)
 //   g*_k(new)   = (1 - s) g_k + dt omega_k R(x)                 (Eq. (BGK-LB-Evolution))
-// Delta and the deviations are O(dx) and carried in FP32; phi is accumulated in FP64. The
-// neighbour differences delta_k are formed from exact float-pair splits of the FP64 phi values
-// (integer operations only), so no FP64 arithmetic is spent on them.
+// Delta and the deviations are O(dx) and carried in FP32; the neighbour differences are
+// delta_k = (h_k - h) + (l_k - l) in FP32 (exact leading part by Sterbenz for nearby values), and
+// the moment update phi_new = h + (l + Delta) is accumulated in FP64 and re-split.
 //
 // The adjoint uses the same kernel with the reverse pull (x + e_k), no source, and the weighted
-// adjoint variable zeta_k = omega_k W + eps_k (W in FP64, eps in FP32); W_new is accumulated into
-// dL/dR(x) += dt W_new.
+// adjoint variable zeta_k = omega_k W + eps_k (W a double-float pair, eps in FP32); W_new is
+// accumulated into dL/dR(x) += dt W_new.
 #include "lhe_internal.h"
 #include "lhe_sites.cuh"
 
 namespace lhe {
 
 template <int D, bool ADJ, bool INTERIOR, bool S2>
-__global__ void __launch_bounds__(256) k_step_dev(const StepArgs a) {
+__global__ void __launch_bounds__(LHE_STEP_THREADS) k_step_dev(const StepArgs a) {
   constexpr Lattice<D> L{};
   constexpr int Q = Lattice<D>::Q;
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -31,12 +32,10 @@ __global__ void __launch_bounds__(256) k_step_dev(const StepArgs a) {
   axis_offsets<D, INTERIOR>(a.g, x, om, op);
   const float *__restrict__ src = static_cast<const float *>(a.src);
   float *__restrict__ dst = static_cast<float *>(a.dst);
-  const double *__restrict__ phis = a.phi_src;
+  const float2 *__restrict__ phis = a.phi_src;
   const int64_t S = a.g.S;
 
-  const double phi0 = __ldg(phis + site);
-  float h0, l0;
-  split_pair(phi0, h0, l0);
+  const float2 p0 = __ldg(phis + site);
   float dl[Q], gk[Q];
   float accw = 0.0f, accg = 0.0f;
 #pragma unroll
@@ -46,16 +45,15 @@ __global__ void __launch_bounds__(256) k_step_dev(const StepArgs a) {
     if (k == 0) {
       dl[k] = 0.0f;
     } else {
-      float hk, lk;
-      split_pair(__ldg(phis + o), hk, lk);
-      dl[k] = (hk - h0) + (lk - l0);
+      const float2 pk = __ldg(phis + o);
+      dl[k] = (pk.x - p0.x) + (pk.y - p0.y);
     }
     accw = fmaf(a.omega_f[k], dl[k], accw);
     accg += gk[k];
   }
   const float Delta = accw + accg;
-  const double phin = phi0 + (double)Delta;
-  a.phi_dst[site] = phin;
+  const double phin = (double)p0.x + (double)(p0.y + Delta);
+  a.phi_dst[site] = df_split(phin);
   if (ADJ && a.gR) a.gR[site] = fma(a.dt, phin, a.gR[site]);
   float dtR = 0.0f;
   const bool field = !ADJ && a.Rfield != nullptr;
@@ -73,7 +71,7 @@ __global__ void __launch_bounds__(256) k_step_dev(const StepArgs a) {
 template <int D, bool ADJ, bool INTERIOR>
 static cudaError_t launch_step_dev_t(const StepArgs &a, cudaStream_t st) {
   if (a.nwork <= 0) return cudaSuccess;
-  const int threads = 256;
+  const int threads = LHE_STEP_THREADS;
   const unsigned blocks = (unsigned)((a.nwork + threads - 1) / threads);
   if (a.s == 2.0)
     k_step_dev<D, ADJ, INTERIOR, true><<<blocks, threads, 0, st>>>(a);

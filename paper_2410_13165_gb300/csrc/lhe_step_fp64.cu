@@ -15,7 +15,7 @@
 namespace lhe {
 
 template <int D, bool ADJ, bool INTERIOR, bool S2>
-__global__ void __launch_bounds__(256) k_step_fp64(const StepArgs a) {
+__global__ void __launch_bounds__(LHE_STEP_THREADS) k_step_fp64(const StepArgs a) {
   constexpr Lattice<D> L{};
   constexpr int Q = Lattice<D>::Q;
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -32,12 +32,17 @@ __global__ void __launch_bounds__(256) k_step_fp64(const StepArgs a) {
   for (int k = 0; k < Q; ++k) f[k] = __ldg(src + k * S + source_site<D, ADJ>(L, k, site, om, op));
   double psi;
   if (ADJ) {
-    const double w = fixed_moment_sum<Q>(f, 1.0, 0.0);
-    psi = (S2 ? 2.0 : a.s) * w;
-    if (a.gR) a.gR[site] = fma(a.dt, w, a.gR[site]);
+    if (S2) {
+      psi = fixed_moment_sum<Q, 1>(f);  // 2 w
+      if (a.gR) a.gR[site] = fma(a.half_dt, psi, a.gR[site]);
+    } else {
+      const double w = fixed_moment_sum<Q, 0>(f);
+      psi = a.s * w;
+      if (a.gR) a.gR[site] = fma(a.dt, w, a.gR[site]);
+    }
   } else {
     const double add = a.Rfield ? a.dt * __ldg(a.Rfield + site) : a.dtR;
-    psi = fixed_moment_sum<Q>(f, S2 ? 2.0 : a.s, add);
+    psi = S2 ? fixed_moment_sum<Q, 1>(f) + add : fma(a.s, fixed_moment_sum<Q, 0>(f), add);
   }
 #pragma unroll
   for (int k = 0; k < Q; ++k) {
@@ -57,13 +62,13 @@ __global__ void __launch_bounds__(256) k_macro_fp64(const StepArgs a, double *__
   for (int k = 0; k < Q; ++k) f[k] = src[k * a.g.S + t];
   const double dtR = a.Rfield ? a.dt * a.Rfield[t] : a.dtR;
   // phi(t_n) = sum_k f*_k(x, t_n) - dt R(x): the collision keeps sum_k f_k and adds dt R.
-  phi[t] = fixed_moment_sum<Q>(f, 1.0, -dtR);
+  phi[t] = fixed_moment_sum<Q, 0>(f) - dtR;
 }
 
 template <int D, bool ADJ, bool INTERIOR>
 static cudaError_t launch_step_fp64_t(const StepArgs &a, cudaStream_t st) {
   if (a.nwork <= 0) return cudaSuccess;
-  const int threads = 256;
+  const int threads = LHE_STEP_THREADS;
   const unsigned blocks = (unsigned)((a.nwork + threads - 1) / threads);
   if (a.s == 2.0)
     k_step_fp64<D, ADJ, INTERIOR, true><<<blocks, threads, 0, st>>>(a);

@@ -1,0 +1,47 @@
+"""bench.py's multi-rank path on CPU: two gloo ranks, barrier and max-over-ranks timing."""
+import os
+import socket
+
+import pytest
+import torch.multiprocessing as mp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank(rank, ws, port, q):
+    import sys
+
+    import torch.distributed as dist
+
+    sys.path.insert(0, ROOT)
+    import bench
+
+    dist.init_process_group("gloo", init_method="tcp://127.0.0.1:%d" % port, rank=rank, world_size=ws)
+    try:
+        bench.barrier(ws, cuda=False)
+        ms = bench.barrier_max(10.0 + 5.0 * rank, ws, device="cpu")
+        q.put((rank, ms, bench.whole_job_mlups(1000, ws, ms)))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_rank_timing_takes_the_slowest_rank():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    ps = [ctx.Process(target=_rank, args=(r, 2, port, q)) for r in range(2)]
+    for p in ps:
+        p.start()
+    for p in ps:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    got = sorted(q.get(timeout=5) for _ in range(2))
+    assert [g[1] for g in got] == [15.0, 15.0]
+    # whole job: 2 ranks x 1000 updates in 15 ms
+    assert abs(got[0][2] - 2 * 1000 / 15e-3 / 1e6) < 1e-12

@@ -182,6 +182,24 @@ LHE_API lhe_status lhe_lbm_macro(lhe_lbm *lbm, double *phi_dev);
  * Returns LHE_ERR_NONFINITE when [3] > 0. */
 LHE_API lhe_status lhe_lbm_diagnostics(lhe_lbm *lbm, double *out_host);
 
+/* Diagnostics of a caller-owned FP64 state without allocating device memory (the paper has no
+ * counterpart; this is a library service). For callers that cannot allocate at this point: code
+ * whose device memory comes from a framework's allocator or a fixed budget, or that runs where the
+ * CUDA runtime refuses cudaMalloc. It creates no handle and calls no allocating routine; its only
+ * scratch memory is a 128 KiB array compiled into the library (one per device, alive until exit).
+ *   p       : the lattice (d, n, lo, hi, bc, c, u, tau, R, m4 settings, stream); precision must be
+ *             LHE_FP64. At most 268435456 nodes (4096 blocks of 65536 nodes fill the scratch array);
+ *             larger lattices are rejected with LHE_ERR_ARG before anything is launched.
+ *   pop_dev : Q*S post-collision FP64 populations, k-major (what lhe_lbm_get_state writes for an
+ *             LHE_FP64 handle); R_dev: per-site source (S doubles) or NULL for the constant p->R.
+ *   out_dev : 4 doubles of device memory receiving the values of lhe_lbm_diagnostics, in order.
+ * Asynchronous on p->stream. The first call on a device resolves the scratch array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture. Every call overwrites
+ * the same scratch array, so calls whose kernels overlap on the GPU (other streams or threads) race;
+ * order them on one stream. */
+LHE_API lhe_status lhe_lbm_diagnostics_noalloc(const lhe_lbm_params *p, const double *pop_dev, const double *R_dev,
+                                               double *out_dev);
+
 /* Copy the forward state (post-collision populations, and phi for LHE_FP32_DEV) to/from a
  * caller buffer of info.state_bytes bytes (device or host memory; cudaMemcpyKind default), for
  * checkpoint/restart. set_state also sets the step index. */

@@ -28,6 +28,7 @@ EXPORTS = [
     "lhe_lbm_destroy", "lhe_lbm_last_error", "lhe_lbm_info", "lhe_lbm_set_stream", "lhe_lbm_init",
     "lhe_lbm_set_boundary_wave", "lhe_lbm_step", "lhe_lbm_macro", "lhe_lbm_diagnostics", "lhe_lbm_get_state",
     "lhe_lbm_set_state", "lhe_lbm_adjoint_seed", "lhe_lbm_adjoint_step", "lhe_lbm_adjoint_grads",
+    "lhe_lbm_diagnostics_noalloc",
 ]
 
 
@@ -103,6 +104,7 @@ def load(path: str | None = None):
         "lhe_lbm_adjoint_seed": (st, [_H, _D]),
         "lhe_lbm_adjoint_step": (st, [_H, ctypes.c_int64]),
         "lhe_lbm_adjoint_grads": (st, [_H, _D, _D, _D]),
+        "lhe_lbm_diagnostics_noalloc": (st, [ctypes.POINTER(lhe_lbm_params), _D, _D, _D]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -207,3 +209,8 @@ def lhe_lbm_adjoint_step(h, n: int) -> None:
 
 def lhe_lbm_adjoint_grads(h, gphi0_ptr: int, ggrad_ptr: int | None, gR_ptr: int | None) -> None:
     check(load().lhe_lbm_adjoint_grads(h, gphi0_ptr, ggrad_ptr, gR_ptr), h)
+
+
+def lhe_lbm_diagnostics_noalloc(p: lhe_lbm_params, pop_ptr: int, R_ptr: int | None, out_ptr: int) -> None:
+    """Diagnostics of a caller-owned FP64 state into 4 device doubles, with no device allocation."""
+    check(load().lhe_lbm_diagnostics_noalloc(ctypes.byref(p), pop_ptr, R_ptr, out_ptr))

@@ -196,6 +196,8 @@ lhe_status check_handle(lhe_lbm *l) {
 
 }  // namespace
 
+lhe_status lhe::record_error(lhe_status status, const std::string &msg) { return fail(nullptr, status, msg); }
+
 extern "C" {
 
 int32_t lhe_lbm_abi_version(void) { return LHE_ABI_VERSION; }

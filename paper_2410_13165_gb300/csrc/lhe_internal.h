@@ -116,6 +116,9 @@ cudaError_t launch_adjoint_seed(int d, bool dev, const Geom &g, const double *om
 cudaError_t launch_df_to_double(const float2 *src, double *dst, int64_t n, cudaStream_t st);
 cudaError_t launch_adjoint_grads(int d, bool dev, const AdjGradArgs &a, cudaStream_t st);
 
+// Record the message lhe_lbm_last_error(NULL) returns on this thread; returns `status`.
+lhe_status record_error(lhe_status status, const std::string &msg);
+
 }  // namespace lhe
 
 // The opaque handle of the C ABI.

@@ -92,7 +92,7 @@ class ClockSampler:
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -349,20 +349,182 @@ def run_ours(args):
     return 0
 
 
+# ------------------------------------------------------------------------------------------------
+# Other workloads of the same path (each prints one JSON line; the default is the line above).
+
+def _timed(fn, steps, warmup=3):
+    import torch
+
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(steps):
+        fn()
+    b.record()
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / steps
+
+
+def run_d4q33_dirichlet(args):
+    """Example 3's 4D box [-1, 1]^4 (64^4 nodes), phi = sin(pi sum_i (x_i - u_i t)): full-way at
+    u = (0.05, 0.2, 0.08, 0.1) and half-way at u = 1e-3 (1,1,1,1), order-4 boundaries, K = 3 init."""
+    import torch
+
+    from paper_2410_13165_gb300 import LBM, build
+    from paper_2410_13165_gb300 import workloads as W
+
+    build.build()
+    n = args.n if args.n != 256 else 64
+    out = {"metric": "MLUPS, D4Q33 %d^4 Dirichlet box" % n, "unit": UNIT, "dtype": "f64", "data": "synthetic"}
+    for bc, u in (("fullway", (0.05, 0.2, 0.08, 0.1)), ("halfway", (1e-3,) * 4)):
+        dx = 2.0 / ((n - 1) if bc == "fullway" else n)
+        X = W.node_coords(4, n, -1.0, dx, halfway=(bc == "halfway"))
+        arg = np.pi * X.sum(axis=0)
+        phi0 = torch.from_numpy(np.sin(arg)).cuda()
+        grad = torch.from_numpy(np.repeat((np.pi * np.cos(arg))[None, :], 4, axis=0).ravel()).cuda()
+        sim = LBM(4, n, -1.0, 1.0, u=u, bc=bc)
+        sim.init(phi0, grad)
+        sim.set_boundary_wave([1.0], [[np.pi] * 4], [0.0])
+        ms = _timed(lambda: sim.step(1), args.steps)
+        T = sim.step_index * sim.dt
+        exact = np.sin(np.pi * (X - np.asarray(u)[:, None] * T).sum(axis=0))
+        err = float(np.sqrt(np.mean((sim.macro().cpu().numpy() - exact) ** 2)))
+        out[bc] = {"mlups": n ** 4 / (ms * 1e-3) / 1e6, "ms_per_step": ms, "boundary_nodes": sim.n_boundary,
+                   "boundary_fraction": sim.n_boundary / n ** 4, "steps_run": sim.step_index, "t_final": T,
+                   "rmse_vs_exact": err,
+                   "gbs_interior_equiv": 528 * n ** 4 / (ms * 1e-3) / 1e9}
+        sim.close()
+        del phi0, grad
+    print(json.dumps(out))
+    return 0
+
+
+def run_d5q51_fp32dev(args):
+    """D5Q51 24^5 periodic (7.96 M nodes): FP32-deviation vs FP64 MLUPS, and the FP32-deviation
+    error against the FP64 path (which matches the oracle to 1e-13) after 2000 steps."""
+    import torch
+
+    from paper_2410_13165_gb300 import LBM, build
+    from paper_2410_13165_gb300 import workloads as W
+
+    build.build()
+    n, T = 24, 2000
+    u = (0.02, 0.04, 0.06, 0.08, 0.1)
+    X = W.node_coords(5, n, 0.0, 1.0 / n)
+    F = W.fourier_field(5, NMODES, SEED + 3)
+    phi0 = torch.from_numpy(F.value(X)).cuda()
+    grad = torch.from_numpy(np.ascontiguousarray(F.grad(X)).ravel()).cuda()
+    res, phis = {}, {}
+    for prec, bps in (("fp64", 816), ("fp32dev", 424)):
+        sim = LBM(5, n, u=u, precision=prec)
+        sim.init(phi0, grad)
+        ms = _timed(lambda: sim.step(1), args.steps)
+        sim.init(phi0, grad)
+        sim.step(T)
+        phis[prec] = sim.macro().cpu().numpy()
+        res[prec] = {"mlups": n ** 5 / (ms * 1e-3) / 1e6, "ms_per_step": ms,
+                     "gbs": bps * n ** 5 / (ms * 1e-3) / 1e9, "bytes_per_site": bps}
+        sim.close()
+    peak, _ = measured_peaks()
+    for v in res.values():
+        v["frac_of_hbm"] = v["gbs"] / peak
+    err = float(np.max(np.abs(phis["fp32dev"] - phis["fp64"])) / np.max(np.abs(phis["fp64"])))
+    print(json.dumps({"metric": "MLUPS, D5Q51 24^5 periodic: FP64 vs FP32-deviation", "unit": UNIT,
+                      "forms": res, "ratio_fp32dev_over_fp64": res["fp32dev"]["mlups"] / res["fp64"]["mlups"],
+                      "rel_maxnorm_err_fp32dev_vs_fp64_after_%d_steps" % T: err}))
+    return 0
+
+
+def run_adjoint_ratio(args):
+    """The differentiation workload: D3Q19 128^3, FP32-deviation forward, T = 1024, loss
+    1/2 |phi(T) - target|^2, gradients w.r.t. phi0 and R(x) through torch.autograd."""
+    import torch
+
+    from paper_2410_13165_gb300 import LBM, build
+    from paper_2410_13165_gb300 import workloads as W
+    from paper_2410_13165_gb300.autograd import lbm_loss
+
+    build.build()
+    n, T = 128, 1024
+    X = W.node_coords(3, n, 0.0, 1.0 / n)
+    phi0 = torch.from_numpy(W.fourier_field(3, NMODES, SEED).value(X)).cuda()
+    R = torch.from_numpy(0.1 * W.fourier_field(3, 4, SEED + 10).value(X)).cuda()
+    target = torch.from_numpy(W.fourier_field(3, 8, SEED + 11).value(X)).cuda()
+    sim = LBM(3, n, u=U, precision="fp32dev")
+    times = {"forward": [], "backward": []}
+    for rep in range(3):
+        p, r = phi0.clone().requires_grad_(True), R.clone().requires_grad_(True)
+        torch.cuda.synchronize()
+        a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        a.record()
+        loss = lbm_loss(p, r, sim, T, target)
+        b.record()
+        loss.backward()
+        c.record()
+        torch.cuda.synchronize()
+        if rep:
+            times["forward"].append(a.elapsed_time(b))
+            times["backward"].append(b.elapsed_time(c))
+    fw, bw = float(np.mean(times["forward"])), float(np.mean(times["backward"]))
+    print(json.dumps({"metric": "adjoint/forward time ratio, D3Q19 128^3 FP32-deviation, T=1024", "unit": "ratio",
+                      "value": bw / fw, "forward_ms": fw, "backward_ms": bw, "loss": float(loss),
+                      "note": "the scheme is affine in the state: the backward pass is T adjoint steps with no recomputation"}))
+    sim.close()
+    return 0
+
+
+def run_convergence(args):
+    """Convergence slopes on the GPU at tau = 1/2 (periodic, K = 3): D2Q9 N = 16..128 (4 modes) and
+    D3Q19 N = 32..256 (8 modes), FP64 and FP32-deviation; T = 1 (steps = N)."""
+    import torch
+
+    from paper_2410_13165_gb300 import LBM, build
+    from paper_2410_13165_gb300 import workloads as W
+
+    build.build()
+    out = {"metric": "RMSE and convergence slopes vs the exact solution, tau = 1/2, T = 1", "unit": "rate"}
+    for d, Ns, u, modes in ((2, (16, 32, 64, 128), (0.1, 0.2), 4), (3, (32, 64, 128, 256), U, NMODES)):
+        for prec in ("fp64", "fp32dev"):
+            errs = []
+            for N in Ns:
+                X = W.node_coords(d, N, 0.0, 1.0 / N)
+                F = W.fourier_field(d, modes, SEED + 20 + d)
+                sim = LBM(d, N, u=u, precision=prec)
+                sim.init(torch.from_numpy(F.value(X)).cuda(), torch.from_numpy(np.ascontiguousarray(F.grad(X)).ravel()).cuda())
+                sim.step(N)
+                exact = F.value(X, shift=np.asarray(u) * 1.0)
+                errs.append(float(np.sqrt(np.mean((sim.macro().cpu().numpy() - exact) ** 2))))
+                sim.close()
+            out["D%dQ%d_%s" % (d, 2 * d * d + 1, prec)] = {
+                "N": list(Ns), "rmse": errs, "slopes": [float(np.log2(a / b)) for a, b in zip(errs, errs[1:])]}
+    print(json.dumps(out))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-baseline", type=int, default=1)
     ap.add_argument("--cpu-n", type=int, default=128)
-    ap.add_argument("--cpu-steps", type=int, default=40)
+    ap.add_argument("--cpu-steps", type=int, default=300)
+    ap.add_argument("--workload", default="d3q19_256",
+                    choices=["d3q19_256", "d4q33_dirichlet", "d5q51_fp32dev", "adjoint", "convergence"])
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    others = {"d4q33_dirichlet": run_d4q33_dirichlet, "d5q51_fp32dev": run_d5q51_fp32dev,
+              "adjoint": run_adjoint_ratio, "convergence": run_convergence}
+    if args.workload in others:
+        if args.steps == 400:
+            args.steps = 50
+        return others[args.workload](args)
     return run_ours(args)
 
 

@@ -1,0 +1,64 @@
+"""Fourth-order convergence of the CUDA path itself (tau = 1/2, K = 3, periodic, T = 1 = N steps),
+against the exact solution phi0(x - u t): the rates Table 2 and Table 3 report (CR ~ 4)."""
+import numpy as np
+import pytest
+
+from paper_2410_13165_gb300 import LBM, build, workloads as W
+from paper_2410_13165_gb300 import _abi
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    build.build()
+    _abi.load()
+
+
+def _errors(d, Ns, u, precision, modes=4, seed=30):
+    import torch
+
+    errs = []
+    for N in Ns:
+        X = W.node_coords(d, N, 0.0, 1.0 / N)
+        F = W.fourier_field(d, modes, seed)
+        sim = LBM(d, N, u=u, precision=precision)
+        sim.init(torch.from_numpy(F.value(X)).cuda(), torch.from_numpy(np.ascontiguousarray(F.grad(X)).ravel()).cuda())
+        sim.step(N)
+        exact = F.value(X, shift=np.asarray(u, dtype=float))
+        errs.append(float(np.sqrt(np.mean((sim.macro().cpu().numpy() - exact) ** 2))))
+        sim.close()
+    return [np.log2(a / b) for a, b in zip(errs, errs[1:])]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32dev"])
+def test_d2q9_fourth_order(precision):
+    sl = _errors(2, (16, 32, 64, 128), (0.1, 0.2), precision)
+    assert all(3.6 < s < 4.6 for s in sl), sl
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32dev"])
+def test_d3q19_fourth_order(precision):
+    sl = _errors(3, (16, 32, 64), (0.1, 0.1, 0.1), precision, modes=8, seed=31)
+    assert all(3.5 < s < 4.7 for s in sl), sl
+
+
+def test_tau_08_is_first_order():
+    """With s != 2 the scheme loses the acoustic-scaling accuracy (the paper needs s = 2)."""
+    import torch
+
+    errs = []
+    for N in (16, 32, 64):
+        X = W.node_coords(2, N, 0.0, 1.0 / N)
+        F = W.fourier_field(2, 4, 32)
+        sim = LBM(2, N, u=(0.1, 0.2), tau=0.8)
+        sim.init(torch.from_numpy(F.value(X)).cuda(), torch.from_numpy(np.ascontiguousarray(F.grad(X)).ravel()).cuda())
+        sim.step(N)
+        exact = F.value(X, shift=np.array([0.1, 0.2]))
+        errs.append(float(np.sqrt(np.mean((sim.macro().cpu().numpy() - exact) ** 2))))
+        sim.close()
+    sl = [np.log2(a / b) for a, b in zip(errs, errs[1:])]
+    assert all(0.7 < s < 1.5 for s in sl), sl

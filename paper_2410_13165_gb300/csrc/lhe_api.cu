@@ -1,6 +1,7 @@
 // lhe_api.cu -- host implementation of the C ABI declared in include/lhe_lbm.h.
 #include <cmath>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <new>
 #include <string>
@@ -283,18 +284,24 @@ lhe_status lhe_lbm_create(const lhe_lbm_params *p, lhe_lbm **out) {
   if (e != cudaSuccess) return bail(cuda_fail(l, e, "cudaMalloc(reduction scratch)"));
   l->red_out = l->red_partials + 4 * (size_t)l->red_blocks;
   if (p->bc != LHE_BC_PERIODIC) {
-    std::vector<int32_t> sites;
-    sites.reserve((size_t)(S - l->g.S_interior));
+    // Boundary nodes grouped by face signature (per dimension: interior, low face or high face), so
+    // that the threads of a warp share one set of unknown populations; site order within a group.
+    std::vector<std::pair<int32_t, int32_t>> keyed;
+    keyed.reserve((size_t)(S - l->g.S_interior));
     for (int64_t s = 0; s < S; ++s) {
       int64_t r = s;
-      bool bnd = false;
+      int32_t sig = 0, w3 = 1;
       for (int i = 0; i < p->d; ++i) {
         const int64_t xi = r % p->n[i];
         r /= p->n[i];
-        if (xi == 0 || xi == p->n[i] - 1) bnd = true;
+        sig += w3 * (xi == 0 ? 1 : (xi == p->n[i] - 1 ? 2 : 0));
+        w3 *= 3;
       }
-      if (bnd) sites.push_back((int32_t)s);
+      if (sig) keyed.emplace_back(sig, (int32_t)s);
     }
+    std::sort(keyed.begin(), keyed.end());
+    std::vector<int32_t> sites(keyed.size());
+    for (size_t j = 0; j < keyed.size(); ++j) sites[j] = keyed[j].second;
     l->nb = (int64_t)sites.size();
     e = cudaMalloc(&l->bsites, sizeof(int32_t) * sites.size());
     if (e != cudaSuccess) return bail(cuda_fail(l, e, "cudaMalloc(boundary nodes)"));
@@ -302,6 +309,10 @@ lhe_status lhe_lbm_create(const lhe_lbm_params *p, lhe_lbm **out) {
     if (e != cudaSuccess) return bail(cuda_fail(l, e, "cudaMemcpy(boundary nodes)"));
     e = cudaMalloc(&l->bc_table, sizeof(double) * ((size_t)kMaxModes * kMaxQ * 3 + kMaxModes));
     if (e != cudaSuccess) return bail(cuda_fail(l, e, "cudaMalloc(boundary table)"));
+    int64_t sum_n = 0;
+    for (int i = 0; i < p->d; ++i) sum_n += p->n[i];
+    e = cudaMalloc(&l->bc_axis, sizeof(double) * 2 * (size_t)kMaxModes * (size_t)sum_n);
+    if (e != cudaSuccess) return bail(cuda_fail(l, e, "cudaMalloc(boundary phase table)"));
   }
   *out = l;
   return LHE_OK;
@@ -321,6 +332,7 @@ lhe_status lhe_lbm_destroy(lhe_lbm *l) {
   cudaFree(l->fdgrad);
   cudaFree(l->bsites);
   cudaFree(l->bc_table);
+  cudaFree(l->bc_axis);
   cudaFree(l->red_partials);
   delete l;
   return LHE_OK;
@@ -405,23 +417,79 @@ lhe_status lhe_lbm_set_boundary_wave(lhe_lbm *l, const lhe_wave *w) {
   if (!w) return fail(l, LHE_ERR_ARG, "wave is NULL");
   if (l->p.bc == LHE_BC_PERIODIC) return fail(l, LHE_ERR_STATE, "boundary data on a periodic box");
   if (w->nmodes < 0 || w->nmodes > kMaxModes || w->reserved0 != 0) return fail(l, LHE_ERR_ARG, "nmodes must be in 0..16");
-  const int d = l->p.d, Q = l->Q;
-  std::vector<double> tab((size_t)w->nmodes * Q * 3 + w->nmodes);
+  const int d = l->p.d, Q = l->Q, M = w->nmodes, P = l->p.bc_order;
+  const double dt = l->dt, dx = l->dx, c = l->p.c, R = l->R;
+  // Per (mode, k) coefficients and per-k constants of the boundary schemes (see lhe_boundary.cu):
+  //   full-way: f_k = omega_k [h - C_k - sum_m T_mk cos xi_m]
+  //   half-way: f_k = wp_k lin + K_k + sum_m (U_mk sin xi_m + V_mk cos xi_m) - f*_kbar
+  std::vector<double> tab((size_t)2 * M * Q + 2 * (size_t)Q, 0.0);
+  double gu = 0.0;
+  for (int i = 0; i < d; ++i) gu += w->g[i] * l->p.u[i];
+  for (int k = 0; k < Q; ++k) {
+    int kb = -1;
+    for (int j = 0; j < Q; ++j) {
+      bool opp = true;
+      for (int i = 0; i < d; ++i)
+        if (l->e[j * d + i] != -l->e[k * d + i]) opp = false;
+      if (opp) kb = j;
+    }
+    double ge = 0.0;  // g . e_k
+    for (int i = 0; i < d; ++i) ge += w->g[i] * l->e[k * d + i];
+    const double wp = l->omega[k] + l->omega[kb], wm = l->omega[k] - l->omega[kb];
+    double *kc = &tab[2 * (size_t)M * Q + 2 * (size_t)k];
+    if (l->p.bc == LHE_BC_FULLWAY) {
+      kc[0] = P >= 3 ? 0.5 * dt * (c * ge - gu) : 0.0;  // C_k: -(dt/2)(g.c_k + R - g.u) + (dt/2) R, over omega_k
+    } else {
+      kc[0] = wp;
+      kc[1] = -wp * 0.5 * dx * ge + (P >= 2 ? wp * 0.5 * dt * (2.0 * R - gu) : 0.0);
+    }
+    for (int m = 0; m < M; ++m) {
+      double ke = 0.0, ku = 0.0;
+      for (int i = 0; i < d; ++i) {
+        ke += w->kappa[m * LHE_MAX_DIM + i] * l->e[k * d + i];
+        ku += w->kappa[m * LHE_MAX_DIM + i] * l->p.u[i];
+      }
+      const double A = c * ke, B = -ku, am = w->a[m];
+      double *cf = &tab[2 * ((size_t)m * Q + k)];
+      if (l->p.bc == LHE_BC_FULLWAY) {
+        const double ab = A + B;
+        double T = 0.0;
+        if (P >= 3) T += 0.5 * dt * am * ab;
+        if (P >= 4) T += dt * dt * dt / 24.0 * am * ab * ab * ab;
+        cf[0] = T;
+      } else {
+        double Ps = wp, Qc = 0.0;  // coefficients of sin and cos at the mid-link point x_b
+        if (P >= 2) Qc += wp * 0.5 * dt * B;
+        if (P >= 3) Ps += wp * dt * dt / 8.0 * A * A + wm * dt * dt / 4.0 * A * B;
+        if (P >= 4) Qc += wp * dt * dt * dt / 16.0 * A * A * B + wp * dt * dt * dt / 24.0 * B * B * B +
+                          wm * dt * dt * dt / 8.0 * A * B * B;
+        Ps *= am;
+        Qc *= am;
+        const double alpha = 0.5 * dx * ke;  // xi(x_b) = xi(x) - alpha
+        cf[0] = Ps * std::cos(alpha) + Qc * std::sin(alpha);
+        cf[1] = -Ps * std::sin(alpha) + Qc * std::cos(alpha);
+      }
+    }
+  }
+  // cos/sin of kappa_mi X_i for every mode, axis and node index: the phase of a node is the product
+  // of its axis factors and the time factor exp(i (theta_m - kappa_m . u t)) of the step.
+  int64_t sum_n = 0;
+  for (int i = 0; i < d; ++i) sum_n += l->p.n[i];
+  std::vector<double> ax((size_t)2 * w->nmodes * sum_n);
   for (int m = 0; m < w->nmodes; ++m) {
-    double ku = 0.0;
-    for (int i = 0; i < d; ++i) ku += w->kappa[m * LHE_MAX_DIM + i] * l->p.u[i];
-    tab[(size_t)w->nmodes * Q * 3 + m] = ku;
-    for (int k = 0; k < Q; ++k) {
-      double ke = 0.0;
-      for (int i = 0; i < d; ++i) ke += w->kappa[m * LHE_MAX_DIM + i] * l->e[k * d + i];
-      const double alpha = 0.5 * l->dx * ke;
-      tab[(m * Q + k) * 3 + 0] = l->p.c * ke;
-      tab[(m * Q + k) * 3 + 1] = std::cos(alpha);
-      tab[(m * Q + k) * 3 + 2] = std::sin(alpha);
+    int64_t off = 0;
+    for (int i = 0; i < d; ++i) {
+      for (int64_t j = 0; j < l->p.n[i]; ++j) {
+        const double arg = w->kappa[m * LHE_MAX_DIM + i] * (l->x0[i] + (double)j * l->dx);
+        ax[2 * ((size_t)m * sum_n + off + j) + 0] = std::cos(arg);
+        ax[2 * ((size_t)m * sum_n + off + j) + 1] = std::sin(arg);
+      }
+      off += l->p.n[i];
     }
   }
   LHE_CK(l, cudaStreamSynchronize(l->stream));
   if (!tab.empty()) LHE_CK(l, cudaMemcpy(l->bc_table, tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice));
+  if (!ax.empty()) LHE_CK(l, cudaMemcpy(l->bc_axis, ax.data(), sizeof(double) * ax.size(), cudaMemcpyHostToDevice));
   l->wave = *w;
   l->have_wave = true;
   return LHE_OK;
@@ -433,6 +501,13 @@ static BoundaryArgs boundary_args(const lhe_lbm *l) {
   b.sites = l->bsites;
   b.nsites = l->nb;
   b.table = l->bc_table;
+  b.axis = l->bc_axis;
+  int32_t off = 0;
+  for (int i = 0; i < l->p.d; ++i) {
+    b.axis_off[i] = off;
+    off += (int32_t)l->p.n[i];
+  }
+  b.axis_len = off;
   for (int k = 0; k < l->Q; ++k) b.omega[k] = l->omega[k];
   b.s = l->s;
   b.oms = 1.0 - l->s;
@@ -482,6 +557,12 @@ lhe_status lhe_lbm_step(lhe_lbm *l, int64_t n) {
       b.phi_src = a.phi_src;
       b.phi_dst = a.phi_dst;
       b.t_eval = (double)(l->p.bc == LHE_BC_FULLWAY ? l->step + 1 : l->step) * l->dt;
+      for (int m = 0; m < l->wave.nmodes; ++m) {
+        double ph = l->wave.theta[m];
+        for (int i = 0; i < d; ++i) ph -= l->wave.kappa[m * LHE_MAX_DIM + i] * l->p.u[i] * b.t_eval;
+        b.ph_c[m] = std::cos(ph);
+        b.ph_s[m] = std::sin(ph);
+      }
       e = launch_boundary(d, l->p.bc, dev, b, l->stream);
       if (e != cudaSuccess) return cuda_fail(l, e, "boundary kernel launch");
     }

@@ -12,10 +12,15 @@
 //                       - (dt^3/16) c c:grad^2 phi_t - (dt^3/24) phi_ttt]
 //                       - (w_k - w_kbar)[(dt^2/4) c.grad phi_t + (dt^3/8) c.grad phi_tt]   (terms by order)
 // then the node collides like the bulk. The Dirichlet data phi = h come from the exact-solution
-// family h = b + R t + g.(x - u t) + sum_m a_m sin(kappa_m.(x - u t) + theta_m); along c_k every
-// derivative d_t^q (c_k.grad)^p of a mode is a_m A^p B^q sin^(p+q)(xi) with A = kappa_m.c_k,
-// B = -kappa_m.u. The half-way evaluation point is reached by rotating (sin, cos) of the node's
-// phase by alpha = (dx/2) kappa_m.e_k (tabulated on the host).
+// family h = b + R t + g.(x - u t) + sum_m a_m sin(xi_m), xi_m = kappa_m.(x - u t) + theta_m. Along
+// c_k every derivative d_t^q (c_k.grad)^p of a mode is a_m A^p B^q sin^(p+q)(xi_m), A = kappa_m.c_k,
+// B = -kappa_m.u, so each scheme is, per unknown k, a node value plus sum_m (U_mk sin xi_m + V_mk
+// cos xi_m) with coefficients that depend only on (m, k), the order and the lattice; the host
+// tabulates them (the half-way shift to x_b is the rotation of (sin, cos) by (dx/2) kappa_m.e_k,
+// folded into U and V). Full-way: f_k = omega_k [h(x) - C_k - sum_m T_mk cos xi_m]; half-way:
+// f_k = wp_k lin(x) + K_k + sum_m (U_mk sin xi_m + V_mk cos xi_m) - f*_kbar(x), lin = linear part of h.
+// The phase xi_m at a node is assembled from tabulated per-axis factors; boundary nodes come
+// grouped by face signature so that a warp shares one set of unknown populations.
 #include "lhe_internal.h"
 
 namespace lhe {
@@ -47,21 +52,30 @@ __global__ void __launch_bounds__(128) k_boundary(const BoundaryArgs a) {
   for (int i = 0; i < D; ++i) X[i] = a.x0[i] + (double)x[i] * a.dx;
   const double te = a.t_eval;
   const int M = a.nmodes;
+  // (cos, sin) of xi_m = theta_m - kappa_m . u t + sum_i kappa_mi X_i: the step's time factor times the
+  // node's per-axis factors (tabulated on the host), with no transcendental call per node.
   double sn[kMaxModes], cs[kMaxModes];
   for (int m = 0; m < M; ++m) {
-    double xi = a.theta[m];
+    double c = a.ph_c[m], s = a.ph_s[m];
 #pragma unroll
-    for (int i = 0; i < D; ++i) xi = fma(a.kappa[m * kMaxD + i], X[i] - a.u[i] * te, xi);
-    sincos(xi, &sn[m], &cs[m]);
+    for (int i = 0; i < D; ++i) {
+      const double *t = a.axis + 2 * ((size_t)m * a.axis_len + a.axis_off[i] + x[i]);
+      const double ca = __ldg(t), sa = __ldg(t + 1);
+      const double c2 = fma(c, ca, -s * sa);
+      s = fma(c, sa, s * ca);
+      c = c2;
+    }
+    sn[m] = s;
+    cs[m] = c;
   }
-  double lin0 = a.b + a.R * te, gu = 0.0;
+  double lin0 = a.b + a.R * te;  // linear part of h at (x, t_eval)
 #pragma unroll
-  for (int i = 0; i < D; ++i) {
-    lin0 = fma(a.gl[i], X[i] - a.u[i] * te, lin0);
-    gu = fma(a.gl[i], a.u[i], gu);
-  }
-  const double *ku = a.table + (size_t)a.nmodes * Q * 3;
-  const double dt = a.dt, dt2 = dt * dt, dt3 = dt2 * dt;
+  for (int i = 0; i < D; ++i) lin0 = fma(a.gl[i], X[i] - a.u[i] * te, lin0);
+  const double *coef = a.table;                                 // [m][k][2]
+  const double *kconst = a.table + (size_t)2 * a.nmodes * Q;    // [k][2]
+  double H = lin0;  // h(x, t_eval) (full-way)
+  if (KIND == 1)
+    for (int m = 0; m < M; ++m) H = fma(a.a[m], sn[m], H);
 
   const double *__restrict__ fsrc = static_cast<const double *>(a.src);
   const float *__restrict__ gsrc = static_cast<const float *>(a.src);
@@ -82,73 +96,39 @@ __global__ void __launch_bounds__(128) k_boundary(const BoundaryArgs a) {
       v[k] = DEV ? fma(a.omega[k], df_value(a.phi_src[o]), (double)gsrc[k * S + o]) : fsrc[k * S + o];
       continue;
     }
-    double gc = 0.0;  // g . c_k
-#pragma unroll
-    for (int i = 0; i < D; ++i)
-      if (L.e[k][i] != 0) gc += a.gl[i] * (a.c * L.e[k][i]);
     if (KIND == 1) {
-      // full-way at the node, time t + dt
-      double D00 = lin0, D1 = gc + (a.R - gu), D3 = 0.0;  // D1 = (c.grad + d_t) phi, D3 = (c.grad + d_t)^3 phi
-      for (int m = 0; m < M; ++m) {
-        const double A = a.table[(m * Q + k) * 3];
-        const double AB = A - ku[m];
-        D00 = fma(a.a[m], sn[m], D00);
-        D1 = fma(a.a[m] * AB, cs[m], D1);
-        D3 = fma(-a.a[m] * AB * AB * AB, cs[m], D3);
-      }
-      double val;
-      if (a.order == 1) {
-        val = a.omega[k] * D00;
-      } else {
-        val = a.omega[k] * (D00 - 0.5 * dt * D1) + 0.5 * dt * a.omega[k] * a.R;
-        if (a.order >= 4) val = fma(a.omega[k] * dt3 / 24.0, D3, val);
-      }
-      v[k] = val;
+      double acc = H - __ldg(kconst + 2 * k);
+      for (int m = 0; m < M; ++m) acc = fma(-__ldg(coef + 2 * (m * Q + k)), cs[m], acc);
+      v[k] = a.omega[k] * acc;
     } else {
-      // half-way at x_b = x - e_k dx/2, time t
       const int kb = L.opp[k];
-      const double wp = a.omega[k] + a.omega[kb], wm = a.omega[k] - a.omega[kb];
-      double D00 = lin0 - 0.5 * dt * gc, D01 = a.R - gu;
-      double D20 = 0.0, D11 = 0.0, D12 = 0.0, D21 = 0.0, D03 = 0.0;
+      double acc = fma(__ldg(kconst + 2 * k), lin0, __ldg(kconst + 2 * k + 1));
       for (int m = 0; m < M; ++m) {
-        const double *tb = a.table + (m * Q + k) * 3;
-        const double A = tb[0], B = -ku[m];
-        const double sb = sn[m] * tb[1] - cs[m] * tb[2];  // sin(xi - alpha)
-        const double cb = cs[m] * tb[1] + sn[m] * tb[2];  // cos(xi - alpha)
-        const double am = a.a[m];
-        D00 = fma(am, sb, D00);
-        D01 = fma(am * B, cb, D01);
-        D20 = fma(-am * A * A, sb, D20);
-        D11 = fma(-am * A * B, sb, D11);
-        D12 = fma(-am * A * B * B, cb, D12);
-        D21 = fma(-am * A * A * B, cb, D21);
-        D03 = fma(-am * B * B * B, cb, D03);
+        acc = fma(__ldg(coef + 2 * (m * Q + k)), sn[m], acc);
+        acc = fma(__ldg(coef + 2 * (m * Q + k) + 1), cs[m], acc);
       }
-      double Bk = wp * D00;
-      if (a.order >= 2) Bk += 0.5 * dt * wp * D01 + 0.5 * dt * wp * a.R;
-      if (a.order >= 3) Bk += -dt2 / 8.0 * wp * D20 - dt2 / 4.0 * wm * D11;
-      if (a.order >= 4) Bk += -dt3 / 8.0 * wm * D12 - dt3 / 16.0 * wp * D21 - dt3 / 24.0 * wp * D03;
       const double fkb = DEV ? fma(a.omega[kb], df_value(a.phi_src[site]), (double)gsrc[kb * S + site])
                               : fsrc[kb * S + site];
-      v[k] = Bk - fkb;
+      v[k] = acc - fkb;
     }
   }
-  double phi = 0.0;
-#pragma unroll
-  for (int k = 0; k < Q; ++k) phi += v[k];
-  const double psi = a.s * phi + dt * a.R;
+  // collision, as in the bulk: phi = sum_k f_k (fixed-point sum), f*_k = (1 - s) f_k + omega_k (s phi + dt R)
+  const double phi = fixed_moment_sum<Q, 0>(v);
+  const double psi = fma(a.s, phi, a.dt * a.R);
+  const bool s2 = a.s == 2.0;
   if (DEV) {
     float *gdst = static_cast<float *>(a.dst);
 #pragma unroll
     for (int k = 0; k < Q; ++k) {
-      const double fs = fma(a.omega[k], psi, a.oms * v[k]);
-      gdst[k * S + site] = (float)(fs - a.omega[k] * phi);
+      const double fs = s2 ? fma(a.omega[k], psi, -v[k]) : fma(a.omega[k], psi, a.oms * v[k]);
+      gdst[k * S + site] = (float)fma(-a.omega[k], phi, fs);
     }
     a.phi_dst[site] = df_split(phi);
   } else {
     double *fdst = static_cast<double *>(a.dst);
 #pragma unroll
-    for (int k = 0; k < Q; ++k) fdst[k * S + site] = fma(a.omega[k], psi, a.oms * v[k]);
+    for (int k = 0; k < Q; ++k)
+      fdst[k * S + site] = s2 ? fma(a.omega[k], psi, -v[k]) : fma(a.omega[k], psi, a.oms * v[k]);
   }
 }
 

@@ -99,20 +99,21 @@ __host__ __device__ constexpr int ceil_log2(int q) {
 // the Q-1 additions of the moment sum (and the conversion) off the FP64 pipe.
 // Subnormal terms are placed as if their exponent were 0 instead of 1 (an error below 2^-1022 in
 // absolute value); any NaN or infinite term makes the result NaN.
-template <int Q, int P2>
-__device__ __forceinline__ double fixed_moment_sum(const double (&f)[Q]) {
+template <int Q, int P2, class Get>
+__device__ __forceinline__ double fixed_moment_sum_impl(Get f) {
   constexpr int G = 10 - ceil_log2(Q);
   static_assert(G >= 3, "too many terms for a 64-bit accumulator");
   unsigned emf = 0u;  // largest exponent field, in place (bits 20..30 of the high word)
 #pragma unroll
-  for (int k = 0; k < Q; ++k) emf = max(emf, (unsigned)__double2hiint(f[k]) & 0x7FF00000u);
+  for (int k = 0; k < Q; ++k) emf = max(emf, (unsigned)__double2hiint(f(k)) & 0x7FF00000u);
   if (emf == 0x7FF00000u) return __longlong_as_double(0x7FF8000000000000ll);
   emf = max(emf, 0x00100000u);
   long long acc = 0;
 #pragma unroll
   for (int k = 0; k < Q; ++k) {
-    const unsigned hi = (unsigned)__double2hiint(f[k]);
-    const unsigned lo = (unsigned)__double2loint(f[k]);
+    const double fk = f(k);
+    const unsigned hi = (unsigned)__double2hiint(fk);
+    const unsigned lo = (unsigned)__double2loint(fk);
     const unsigned ef = hi & 0x7FF00000u;
     const unsigned mh = (hi & 0x000FFFFFu) | min(ef, 0x00100000u);  // implicit bit unless zero/subnormal
     const unsigned sh = (emf - max(ef, 0x00100000u)) >> 20;
@@ -143,6 +144,11 @@ __device__ __forceinline__ double fixed_moment_sum(const double (&f)[Q]) {
     return __ll2double_rn(acc) * pow2_bits(p1) * pow2_bits(p - p1);
   }
   return __longlong_as_double((long long)(sbit | ((unsigned long long)ex << 52) | (mant & 0xFFFFFFFFFFFFFull)));
+}
+
+template <int Q, int P2>
+__device__ __forceinline__ double fixed_moment_sum(const double (&f)[Q]) {
+  return fixed_moment_sum_impl<Q, P2>([&](int k) { return f[k]; });
 }
 
 // Double-float storage of the macroscopic variable of the FP32-deviation form: phi = h + l with h

@@ -50,6 +50,11 @@ struct BoundaryArgs {
   const float2 *phi_src;
   float2 *phi_dst;
   const double *table;     // per (mode, k): [kc, cos alpha, sin alpha], then ku per mode
+  const double *axis;      // per (mode, axis, node index): [cos, sin] of kappa_mi X_i
+  int32_t axis_off[kMaxD]; // offset of axis i in the per-mode block of `axis`
+  int32_t axis_len;        // sum_i n_i
+  double ph_c[kMaxModes];  // cos and sin of theta_m - kappa_m . u t_eval
+  double ph_s[kMaxModes];
   double omega[kMaxQ];
   double s, oms, R, dt, dx, c;
   double x0[kMaxD];        // coordinate of node 0
@@ -148,6 +153,7 @@ struct lhe_lbm {
   bool have_wave = false;
   lhe_wave wave{};
   double *bc_table = nullptr;
+  double *bc_axis = nullptr;    // per-axis phase tables of the Dirichlet data
   // adjoint
   void *adj[2] = {nullptr, nullptr};
   float2 *adjW[2] = {nullptr, nullptr};

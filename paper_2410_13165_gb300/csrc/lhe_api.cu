@@ -187,7 +187,88 @@ StepArgs step_args(const lhe_lbm *l) {
   a.dt = l->dt;
   a.half_dt = 0.5 * l->dt;
   a.Rfield = l->Rfield;
+  a.collide = kCollideGeneral;
+  a.mu = 1.0 - l->s;
+  a.sig = l->s;
+  a.rho_dt = a.dt;
+  a.rho_dtR = a.dtR;
+  a.gsc = a.dt;
+  a.pscale = 1.0;
   return a;
+}
+
+// ---- scaled representation of the FP64 state (s != 2, periodic boxes) ----
+// With r = 1 - s the collision f*_k = r f_k + omega_k psi costs two FP64 operations per population,
+// twice the s = 2 form. Storing G = K f* with K = r^-j after j consecutive scaled steps turns the
+// step into
+//   G*_k(x) = G_k(x - e_k) + omega_k Psi,   Psi = sig sum_k G_k + K' dt R,   sig = s/r, K' = K/r,
+// one FMA per population and the same map up to rounding (the pulled term r f_k equals G_k / K').
+// sig is one of the three doubles nearest to s/r, chosen every step so that the accumulated
+// relative error of sig r against s stays within about one ulp (error feedback): a fixed rounded
+// quotient would move the conserved mode by s times its rounding error on every step. Before K
+// would pass 2^kScaleBits, one general step with mu = r^(j+1), sig = s r^j returns to K = 1.
+constexpr double kScaleBits = 128.0;
+constexpr double kMinScaledR = 1.0 / 64.0;
+
+bool scaled_eligible(const lhe_lbm *l) {
+  const double r = 1.0 - l->s;
+  return l->p.bc == LHE_BC_PERIODIC && l->p.precision == LHE_FP64 && l->s != 2.0 && std::fabs(r) >= kMinScaledR &&
+         std::fabs(r) <= 1.0 / kMinScaledR && std::fabs(r) != 1.0;
+}
+
+int scaled_run(const lhe_lbm *l) {  // longest run of scaled steps starting from K = 1
+  const double b = std::fabs(std::log2(std::fabs(1.0 - l->s)));
+  return b * 4096.0 <= kScaleBits ? 4096 : (int)std::floor(kScaleBits / b);
+}
+
+double pick_sig(double s, double r, double &acc) {
+  const double c0 = s / r;
+  const double cand[3] = {c0, std::nextafter(c0, -INFINITY), std::nextafter(c0, INFINITY)};
+  double best = c0, best_err = std::fma(c0, r, -s) / s;
+  for (double c : cand) {
+    const double err = std::fma(c, r, -s) / s;  // relative error of c r against s
+    if (std::fabs(acc + err) < std::fabs(acc + best_err)) {
+      best = c;
+      best_err = err;
+    }
+  }
+  acc += best_err;
+  return best;
+}
+
+// Collision constants of the next step of a scaled-eligible state ([0] forward, [1] adjoint).
+void plan_scaled_step(lhe_lbm *l, int which, StepArgs &a) {
+  const double s = l->s, r = 1.0 - s;
+  int32_t &j = l->scale_j[which];
+  const double rj = std::pow(r, (double)j);  // 1/K
+  a.gsc = a.dt * rj;                          // adjoint: dt w = dt r^j sum_k Z_k
+  if (j + 1 > scaled_run(l)) {
+    a.collide = kCollideGeneral;
+    a.mu = std::pow(r, (double)(j + 1));
+    a.sig = s * rj;
+    a.rho_dt = a.dt;
+    a.rho_dtR = a.dtR;
+    j = 0;
+  } else {
+    const double K1 = std::pow(r, -(double)(j + 1));
+    a.collide = kCollideScaled;
+    a.sig = pick_sig(s, r, l->scale_acc[which]);
+    a.rho_dt = a.dt * K1;
+    a.rho_dtR = a.dtR * K1;
+    j += 1;
+  }
+}
+
+// Returns a scaled state to f* in place (rounding once per population) and restarts the error
+// feedback of sig.
+lhe_status unscale(lhe_lbm *l, int which) {
+  int32_t &j = l->scale_j[which];
+  if (j == 0) return LHE_OK;
+  double *p = static_cast<double *>(which == 0 ? l->pop[l->cur] : l->adj[l->acur]);
+  LHE_CK(l, launch_scale_fp64(p, (int64_t)l->Q * l->g.S, std::pow(1.0 - l->s, (double)j), l->stream));
+  j = 0;
+  l->scale_acc[which] = 0.0;  // a state read out and set back continues exactly alike
+  return LHE_OK;
 }
 
 lhe_status check_handle(lhe_lbm *l) {
@@ -408,6 +489,8 @@ lhe_status lhe_lbm_init(lhe_lbm *l, const double *phi0, const double *grad, cons
   l->cur = 0;
   l->step = 0;
   l->initialised = true;
+  l->scale_j[0] = 0;
+  l->scale_acc[0] = 0.0;
   l->adj_ready = false;
   return LHE_OK;
 }
@@ -542,7 +625,9 @@ lhe_status lhe_lbm_step(lhe_lbm *l, int64_t n) {
   StepArgs a = step_args(l);
   BoundaryArgs b{};
   if (!periodic) b = boundary_args(l);
+  const bool scaled = scaled_eligible(l);
   for (int64_t it = 0; it < n; ++it) {
+    if (scaled) plan_scaled_step(l, 0, a);
     a.src = l->pop[l->cur];
     a.dst = l->pop[1 - l->cur];
     a.phi_src = l->phi[l->cur];
@@ -582,6 +667,7 @@ lhe_status lhe_lbm_macro(lhe_lbm *l, double *phi_out) {
   }
   StepArgs a = step_args(l);
   a.src = l->pop[l->cur];
+  if (l->scale_j[0] != 0) a.pscale = std::pow(1.0 - l->s, (double)l->scale_j[0]);
   LHE_CK(l, launch_macro_fp64(l->p.d, a, phi_out, l->stream));
   return LHE_OK;
 }
@@ -590,6 +676,7 @@ lhe_status lhe_lbm_diagnostics(lhe_lbm *l, double *out_host) {
   if (lhe_status s = check_handle(l)) return s;
   if (!out_host) return fail(l, LHE_ERR_ARG, "out_host is NULL");
   if (!l->initialised) return fail(l, LHE_ERR_STATE, "lhe_lbm_diagnostics before lhe_lbm_init");
+  if (lhe_status st = unscale(l, 0)) return st;
   ReduceArgs a{};
   a.g = l->g;
   a.pop = l->pop[l->cur];
@@ -612,6 +699,7 @@ lhe_status lhe_lbm_get_state(lhe_lbm *l, void *buf) {
   if (lhe_status s = check_handle(l)) return s;
   if (!buf) return fail(l, LHE_ERR_ARG, "buf is NULL");
   if (!l->initialised) return fail(l, LHE_ERR_STATE, "no state before lhe_lbm_init");
+  if (lhe_status st = unscale(l, 0)) return st;
   const size_t pb = pop_bytes(l);
   LHE_CK(l, cudaMemcpyAsync(buf, l->pop[l->cur], pb, cudaMemcpyDefault, l->stream));
   if (l->p.precision == LHE_FP32_DEV)
@@ -631,6 +719,8 @@ lhe_status lhe_lbm_set_state(lhe_lbm *l, const void *buf, int64_t step) {
                               cudaMemcpyDefault, l->stream));
   l->step = step;
   l->initialised = true;
+  l->scale_j[0] = 0;
+  l->scale_acc[0] = 0.0;
   return LHE_OK;
 }
 
@@ -651,6 +741,8 @@ lhe_status lhe_lbm_adjoint_seed(lhe_lbm *l, const double *seed) {
   LHE_CK(l, launch_adjoint_seed(l->p.d, dev, l->g, l->omega, seed, l->adj[0], l->adjW[0], l->gR, l->stream));
   l->acur = 0;
   l->adj_ready = true;
+  l->scale_j[1] = 0;
+  l->scale_acc[1] = 0.0;
   return LHE_OK;
 }
 
@@ -663,7 +755,9 @@ lhe_status lhe_lbm_adjoint_step(lhe_lbm *l, int64_t n) {
   a.Rfield = nullptr;
   a.gR = l->gR;
   a.nwork = l->g.S;
+  const bool scaled = scaled_eligible(l);
   for (int64_t it = 0; it < n; ++it) {
+    if (scaled) plan_scaled_step(l, 1, a);
     a.src = l->adj[l->acur];
     a.dst = l->adj[1 - l->acur];
     a.phi_src = l->adjW[l->acur];
@@ -680,6 +774,7 @@ lhe_status lhe_lbm_adjoint_grads(lhe_lbm *l, double *gphi0, double *ggrad, doubl
   if (lhe_status s = check_handle(l)) return s;
   if (!l->adj_ready) return fail(l, LHE_ERR_STATE, "lhe_lbm_adjoint_grads before lhe_lbm_adjoint_seed");
   if (!gphi0) return fail(l, LHE_ERR_ARG, "dL/dphi0 is NULL");
+  if (lhe_status st = unscale(l, 1)) return st;
   const bool dev = l->p.precision == LHE_FP32_DEV;
   const int d = l->p.d;
   AdjGradArgs a{};

@@ -37,8 +37,17 @@ struct StepArgs {
   double s, oms;           // s and 1 - s
   double dtR;              // dt * R (constant source)
   double dt, half_dt;
+  // FP64 collision with s != 2 (see kCollide* in lhe_step_fp64.cu): f*_k = mu f_k + omega_k psi with
+  // psi = sig sum_k f_k + rho_dt R(x) (or + rho_dtR); adjoint: gR += gsc w, psi = sig w.
+  double mu, sig, rho_dt, rho_dtR, gsc;
+  double pscale;           // macro: factor from the stored populations to f* (1 unless scaled)
+  int32_t collide;         // kCollideGeneral / kCollideScaled (s != 2 only)
   int64_t nwork;           // number of sites processed (S, or the interior count)
 };
+
+// FP64 collision forms for s != 2.
+constexpr int kCollideGeneral = 0;  // two FP64 operations per population
+constexpr int kCollideScaled = 1;   // scaled representation, one FMA per population
 
 // Arguments of the boundary-node kernels (Dirichlet boxes).
 struct BoundaryArgs {
@@ -119,6 +128,7 @@ cudaError_t launch_reduce(int d, bool dev, const ReduceArgs &a, int nblocks, cud
 cudaError_t launch_adjoint_seed(int d, bool dev, const Geom &g, const double *omega, const double *seed,
                                 void *adj, float2 *adjW, double *gR, cudaStream_t st);
 cudaError_t launch_df_to_double(const float2 *src, double *dst, int64_t n, cudaStream_t st);
+cudaError_t launch_scale_fp64(double *p, int64_t n, double factor, cudaStream_t st);
 cudaError_t launch_adjoint_grads(int d, bool dev, const AdjGradArgs &a, cudaStream_t st);
 
 // Record the message lhe_lbm_last_error(NULL) returns on this thread; returns `status`.
@@ -160,6 +170,11 @@ struct lhe_lbm {
   double *gR = nullptr;
   int acur = 0;
   bool adj_ready = false;
+  // Scaled representation of the FP64 state when s != 2 on periodic boxes: the stored populations
+  // are K f* with K = (1 - s)^-j; j = 0 means the state is stored as f* itself. [0] forward, [1]
+  // adjoint. acc accumulates the relative error of the rounded s/(1 - s) factors.
+  int32_t scale_j[2] = {0, 0};
+  double scale_acc[2] = {0.0, 0.0};
   // diagnostics
   double *red_partials = nullptr;
   double *red_out = nullptr;

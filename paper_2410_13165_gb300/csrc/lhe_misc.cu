@@ -326,4 +326,17 @@ cudaError_t launch_df_to_double(const float2 *src, double *dst, int64_t n, cudaS
   return cudaGetLastError();
 }
 
+// In-place multiplication of an FP64 population array by a constant (undoes the scaled
+// representation of the state; see lhe_api.cu).
+__global__ void __launch_bounds__(256) k_scale_fp64(double *__restrict__ p, int64_t n, double factor) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) p[i] *= factor;
+}
+
+cudaError_t launch_scale_fp64(double *p, int64_t n, double factor, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_scale_fp64<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(p, n, factor);
+  return cudaGetLastError();
+}
+
 }  // namespace lhe

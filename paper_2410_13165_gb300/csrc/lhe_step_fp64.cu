@@ -4,6 +4,9 @@
 //   f_k(x)  = f*_k(x - e_k)                      (pull; periodic wrap or interior of a Dirichlet box)
 //   phi(x)  = sum_k f_k(x)                       (Eq. (0-1-meq))
 //   f*_k(x) = (1 - s) f_k + omega_k (s phi + dt R(x))      (s = 2: omega_k (2 phi + dt R) - f_k)
+// For s != 2 the stored array may hold the scaled populations G = K f* (K = (1 - s)^-j), updated by
+// G*_k = G_k + omega_k (sig sum_k G_k + K' dt R) with sig ~ s/(1 - s) and K' = K/(1 - s): the factor
+// (1 - s) of the pulled populations is carried by K instead of one multiply per population.
 // Adjoint (transpose of the step, in the weighted variable zeta_k = omega_k nu_k):
 //   mu_k(x) = zeta_k(x + e_k)                    (reverse pull)
 //   w(x)    = sum_k mu_k(x),  gR(x) += dt w(x)
@@ -14,7 +17,10 @@
 
 namespace lhe {
 
-template <int D, bool ADJ, bool INTERIOR, bool S2>
+// Template collision forms: s = 2, general s (mu, sig, rho from StepArgs), scaled representation.
+constexpr int kModeGeneral = 0, kModeS2 = 1, kModeScaled = 2;
+
+template <int D, bool ADJ, bool INTERIOR, int MODE>
 __global__ void __launch_bounds__(LHE_STEP_THREADS) k_step_fp64(const StepArgs a) {
   constexpr Lattice<D> L{};
   constexpr int Q = Lattice<D>::Q;
@@ -32,21 +38,24 @@ __global__ void __launch_bounds__(LHE_STEP_THREADS) k_step_fp64(const StepArgs a
   for (int k = 0; k < Q; ++k) f[k] = __ldg(src + k * S + source_site<D, ADJ>(L, k, site, om, op));
   double psi;
   if (ADJ) {
-    if (S2) {
+    if (MODE == kModeS2) {
       psi = fixed_moment_sum<Q, 1>(f);  // 2 w
       if (a.gR) a.gR[site] = fma(a.half_dt, psi, a.gR[site]);
     } else {
       const double w = fixed_moment_sum<Q, 0>(f);
-      psi = a.s * w;
-      if (a.gR) a.gR[site] = fma(a.dt, w, a.gR[site]);
+      psi = a.sig * w;
+      if (a.gR) a.gR[site] = fma(a.gsc, w, a.gR[site]);
     }
+  } else if (MODE == kModeS2) {
+    psi = fixed_moment_sum<Q, 1>(f) + (a.Rfield ? a.dt * __ldg(a.Rfield + site) : a.dtR);
   } else {
-    const double add = a.Rfield ? a.dt * __ldg(a.Rfield + site) : a.dtR;
-    psi = S2 ? fixed_moment_sum<Q, 1>(f) + add : fma(a.s, fixed_moment_sum<Q, 0>(f), add);
+    psi = fma(a.sig, fixed_moment_sum<Q, 0>(f), a.Rfield ? a.rho_dt * __ldg(a.Rfield + site) : a.rho_dtR);
   }
 #pragma unroll
   for (int k = 0; k < Q; ++k) {
-    const double out = S2 ? fma(a.omega[k], psi, -f[k]) : fma(a.omega[k], psi, a.oms * f[k]);
+    const double out = MODE == kModeS2      ? fma(a.omega[k], psi, -f[k])
+                       : MODE == kModeScaled ? fma(a.omega[k], psi, f[k])
+                                             : fma(a.omega[k], psi, a.mu * f[k]);
     st_stream(dst + k * S + site, out);
   }
 }
@@ -61,8 +70,9 @@ __global__ void __launch_bounds__(256) k_macro_fp64(const StepArgs a, double *__
 #pragma unroll
   for (int k = 0; k < Q; ++k) f[k] = src[k * a.g.S + t];
   const double dtR = a.Rfield ? a.dt * a.Rfield[t] : a.dtR;
-  // phi(t_n) = sum_k f*_k(x, t_n) - dt R(x): the collision keeps sum_k f_k and adds dt R.
-  phi[t] = fixed_moment_sum<Q, 0>(f) - dtR;
+  // phi(t_n) = sum_k f*_k(x, t_n) - dt R(x): the collision keeps sum_k f_k and adds dt R. pscale
+  // converts a scaled state back to f* (1 otherwise, exact).
+  phi[t] = fma(fixed_moment_sum<Q, 0>(f), a.pscale, -dtR);
 }
 
 template <int D, bool ADJ, bool INTERIOR>
@@ -71,9 +81,11 @@ static cudaError_t launch_step_fp64_t(const StepArgs &a, cudaStream_t st) {
   const int threads = LHE_STEP_THREADS;
   const unsigned blocks = (unsigned)((a.nwork + threads - 1) / threads);
   if (a.s == 2.0)
-    k_step_fp64<D, ADJ, INTERIOR, true><<<blocks, threads, 0, st>>>(a);
+    k_step_fp64<D, ADJ, INTERIOR, kModeS2><<<blocks, threads, 0, st>>>(a);
+  else if (a.collide == kCollideScaled)
+    k_step_fp64<D, ADJ, INTERIOR, kModeScaled><<<blocks, threads, 0, st>>>(a);
   else
-    k_step_fp64<D, ADJ, INTERIOR, false><<<blocks, threads, 0, st>>>(a);
+    k_step_fp64<D, ADJ, INTERIOR, kModeGeneral><<<blocks, threads, 0, st>>>(a);
   return cudaGetLastError();
 }
 

@@ -3,21 +3,23 @@
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--n 256]
 
-One benchmark step is one pass of the hot path over the workload: one lattice update of the FP64
-path, one of the FP32-deviation path and one adjoint update (FP32-deviation adjoint with the dL/dR
-accumulation), each a fused stream+collide kernel over all 256^3 nodes. `value` is the FP64 path's
-MLUPS (million lattice-node updates per second, whole job over N GPUs); the other forms are reported
-under "forms". Inputs are resident in HBM and each population buffer (2.5 GB) exceeds the 126 MB L2,
-so no L2 flush is needed between iterations. `e2e` times the same FP64 metric through the public API
-with host buffers: upload of phi0 and grad phi0 from pinned memory, init, 1000 steps (the workload's
-run length), macro and download of phi, per e2e step.
+One benchmark step is one pass of the hot path over the workload: one FP64 lattice update at each
+relaxation time tau in {0.6, 0.8, 1.2}, one update of the FP32-deviation path and one adjoint update
+(FP32-deviation adjoint with the dL/dR accumulation) at tau = 0.8, each a fused stream+collide kernel
+over all 256^3 nodes. `value` is the FP64 path's MLUPS (million lattice-node updates per second,
+whole job over N GPUs) over the three tau; every form is reported under "forms", with tau = 1/2 (the
+s = 2 collision) as an extra line. Inputs are resident in HBM and each population buffer (2.5 GB)
+exceeds the 126 MB L2, so no L2 flush is needed between iterations. `e2e` times the FP64 metric
+through the public API with host buffers: upload of phi0 and grad phi0 from pinned memory, init,
+1000 steps at tau = 0.8 (the workload's run length), macro and download of phi, per e2e step.
 
 Under torchrun (N > 1) every rank runs the workload on its own GPU (independent replicas: the path
 has no data exchange between boxes of one replica), timing is bracketed by a barrier and CUDA
 synchronisation on both sides, and rank 0 reports the max over ranks.
 
 --impl reference times the FP64 CPU oracle (the reference implementation of this paper-only
-repository) on the host cores, one oracle step of the same workload per benchmark step.
+repository) on the host cores: per benchmark step, one oracle step at each tau on a 128^3 sample of
+the workload (--ref-n).
 """
 from __future__ import annotations
 
@@ -39,16 +41,20 @@ METRIC = "MLUPS & HBM GB/s (% of peak), D3Q19 256^3: FP64 vs FP32-mixed vs adjoi
 UNIT = "MLUPS"
 U = (0.1, 0.1, 0.1)
 NMODES, SEED = 8, 2
+TAUS = (0.6, 0.8, 1.2)
+TAU_DEV = 0.8
 BYTES_PER_SITE = {"fp64": 2 * 19 * 8, "fp32dev": 2 * 19 * 4 + 16, "adjoint": 2 * 19 * 4 + 16 + 16}
 E2E_STEPS = 1000
 
 
 def workload(n):
-    return {"workload": "D3Q19 %d^3 periodic, 8 seeded Fourier modes (k in 1..3), u=(0.1,0.1,0.1), tau=0.5 (s=2), R=0" % n,
-            "lattice": "D3Q19", "n": n, "sites": n ** 3, "tau": 0.5, "u": list(U), "modes": NMODES,
-            "step": "one update of each form: fp64, fp32dev, adjoint(fp32dev, with dL/dR)",
+    return {"workload": "D3Q19 %d^3 periodic, 8 seeded Fourier modes (k in 1..3), u=(0.1,0.1,0.1), "
+                        "tau in {0.6, 0.8, 1.2}, R=0" % n,
+            "lattice": "D3Q19", "n": n, "sites": n ** 3, "tau": list(TAUS), "u": list(U), "modes": NMODES,
+            "step": "one fp64 update at each tau, one fp32dev update and one adjoint(fp32dev, with dL/dR) "
+                    "update at tau=%g" % TAU_DEV,
             "l2": "inputs larger than L2 (population buffers 2.5 GB / 1.3 GB)",
-            "e2e_job": "H2D phi0+grad (pinned), init, %d fp64 steps, macro, D2H phi" % E2E_STEPS}
+            "e2e_job": "H2D phi0+grad (pinned), init, %d fp64 steps at tau=%g, macro, D2H phi" % (E2E_STEPS, TAU_DEV)}
 
 
 def measured_peaks():
@@ -178,18 +184,20 @@ def whole_job_mlups(sites_per_rank: int, ws: int, ms_max: float) -> float:
 
 
 def cpu_oracle_mlups(n: int, steps: int, threads: int):
+    """The FP64 oracle on the host cores: `steps` steps at each tau of the workload on n^3 nodes."""
     from oracle import oracle as O
     from paper_2410_13165_gb300 import workloads as W
 
     O.set_threads(threads)
-    m = O.Model(3, n, 0.0, 1.0, U)
     phi0, grad, _, _ = W.periodic_problem(3, n, NMODES, SEED)
-    f = m.init(phi0, grad, 3)
-    f = m.step(f, 0, 1)
-    t0 = time.perf_counter()
-    m.step(f, 1, steps)
-    dt = time.perf_counter() - t0
-    return n ** 3 * steps / dt / 1e6, dt
+    dt = 0.0
+    for tau in TAUS:
+        m = O.Model(3, n, 0.0, 1.0, U, tau=tau)
+        f = m.step(m.init(phi0, grad, 3), 0, 1)
+        t0 = time.perf_counter()
+        m.step(f, 1, steps)
+        dt += time.perf_counter() - t0
+    return len(TAUS) * n ** 3 * steps / dt / 1e6, dt
 
 
 def run_reference(args):
@@ -201,20 +209,24 @@ def run_reference(args):
 
     threads = os.cpu_count() or 1
     O.set_threads(threads)
-    n = args.n
-    m = O.Model(3, n, 0.0, 1.0, U)
+    n = args.ref_n
     phi0, grad, _, _ = W.periodic_problem(3, n, NMODES, SEED)
-    f = m.init(phi0, grad, 3)
-    f = m.step(f, 0, args.warmup)
+    models, states = [], []
+    for tau in TAUS:
+        m = O.Model(3, n, 0.0, 1.0, U, tau=tau)
+        models.append(m)
+        states.append(m.step(m.init(phi0, grad, 3), 0, args.warmup))
     t0 = time.perf_counter()
-    f = m.step(f, args.warmup, args.steps)
+    for i, m in enumerate(models):
+        states[i] = m.step(states[i], args.warmup, args.steps)
     dt = time.perf_counter() - t0
-    mlups = n ** 3 * args.steps / dt / 1e6
+    mlups = len(TAUS) * n ** 3 * args.steps / dt / 1e6
     line = {"metric": METRIC, "value": mlups, "unit": UNIT, "impl": "reference", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload(n),
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload(args.n),
             "cpu_baseline": {"value": mlups, "unit": UNIT, "cores": threads, "kind": "oracle",
-                             "sample": "FP64 CPU oracle, one step of the D3Q19 %d^3 workload per benchmark step" % n},
+                             "sample": "FP64 CPU oracle; per benchmark step one oracle step at each tau in "
+                                       "{0.6, 0.8, 1.2} on a D3Q19 %d^3 sample of the workload" % n},
             "e2e": {"value": mlups, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -238,32 +250,34 @@ def run_ours(args):
     grad = torch.from_numpy(np.ascontiguousarray(grad_np).ravel()).to(dev)
     del X
 
-    sims = {"fp64": LBM(3, n, u=U, tau=0.5), "fp32dev": LBM(3, n, u=U, tau=0.5, precision="fp32dev")}
-    adj = LBM(3, n, u=U, tau=0.5, precision="fp32dev")
+    fp64_names = ["fp64_tau%g" % t for t in TAUS]
+    sims = {name: LBM(3, n, u=U, tau=t) for name, t in zip(fp64_names, TAUS)}
+    sims["fp32dev"] = LBM(3, n, u=U, tau=TAU_DEV, precision="fp32dev")
+    adj = LBM(3, n, u=U, tau=TAU_DEV, precision="fp32dev")
     for s in sims.values():
         s.init(phi0, grad)
     adj.init(phi0, grad)
     adj.step(1)
     adj.adjoint_seed(adj.macro())
     stream = torch.cuda.current_stream()
+    order = fp64_names + ["fp32dev"]
 
     def one_pass(ev=None):
+        for i, name in enumerate(order):
+            if ev:
+                ev[i].record(stream)
+            sims[name].step(1)
         if ev:
-            ev[0].record(stream)
-        sims["fp64"].step(1)
-        if ev:
-            ev[1].record(stream)
-        sims["fp32dev"].step(1)
-        if ev:
-            ev[2].record(stream)
+            ev[len(order)].record(stream)
         adj.adjoint_step(1)
         if ev:
-            ev[3].record(stream)
+            ev[len(order) + 1].record(stream)
 
     for _ in range(max(args.warmup, 3)):
         one_pass()
     K = args.steps
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(K)]
+    nev = len(order) + 2
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(nev)] for _ in range(K)]
     barrier(ws)
     with ClockSampler(local) as clk:
         t_start = torch.cuda.Event(enable_timing=True)
@@ -274,19 +288,32 @@ def run_ours(args):
         t_end.record(stream)
         barrier(ws)
     total_ms = t_start.elapsed_time(t_end)
-    per = {"fp64": 0.0, "fp32dev": 0.0, "adjoint": 0.0}
+    names = order + ["adjoint"]
+    per = {name: 0.0 for name in names}
     for k in range(K):
-        per["fp64"] += evs[k][0].elapsed_time(evs[k][1])
-        per["fp32dev"] += evs[k][1].elapsed_time(evs[k][2])
-        per["adjoint"] += evs[k][2].elapsed_time(evs[k][3])
+        for i, name in enumerate(names):
+            per[name] += evs[k][i].elapsed_time(evs[k][i + 1])
     per = {k: barrier_max(v / K, ws) for k, v in per.items()}
+    per["fp64"] = sum(per[nm] for nm in fp64_names) / len(fp64_names)  # mean update time over the tau set
     total_ms = barrier_max(total_ms, ws)
     peak, peak_kind = measured_peaks()
     forms = {}
     for name, ms in per.items():
-        gbs = BYTES_PER_SITE[name] * S / (ms * 1e-3) / 1e9
+        bps = BYTES_PER_SITE["fp64" if name.startswith("fp64") else name]
+        gbs = bps * S / (ms * 1e-3) / 1e9
         forms[name] = {"mlups": whole_job_mlups(S, ws, ms), "ms_per_lb_step": ms, "gbs_per_gpu": gbs,
-                       "frac_of_hbm": gbs / peak, "bytes_per_site": BYTES_PER_SITE[name]}
+                       "frac_of_hbm": gbs / peak, "bytes_per_site": bps}
+    forms["fp64"]["tau"] = list(TAUS)
+    forms["fp32dev"]["tau"] = forms["adjoint"]["tau"] = TAU_DEV
+    # the s = 2 collision (tau = 1/2) outside the timed pass, for reference
+    half = LBM(3, n, u=U, tau=0.5)
+    half.init(phi0, grad)
+    ms_half = barrier_max(_timed(lambda: half.step(1), 50), ws)
+    half.close()
+    gbs = BYTES_PER_SITE["fp64"] * S / (ms_half * 1e-3) / 1e9
+    forms["fp64_tau0.5"] = {"mlups": whole_job_mlups(S, ws, ms_half), "ms_per_lb_step": ms_half, "gbs_per_gpu": gbs,
+                            "frac_of_hbm": gbs / peak, "bytes_per_site": BYTES_PER_SITE["fp64"],
+                            "note": "s = 2 collision, timed separately (50 steps)"}
     fp64 = forms["fp64"]
     kernel_src = os.path.join(ROOT, "paper_2410_13165_gb300", "csrc", "lhe_step_fp64.cu")
     traffic = profiled_traffic(kernel_src)
@@ -299,7 +326,7 @@ def run_ours(args):
         h_out = torch.empty(S, dtype=torch.float64).pin_memory()
         d_phi0 = torch.empty_like(phi0)
         d_grad = torch.empty_like(grad)
-        sim = sims["fp64"]
+        sim = sims["fp64_tau%g" % TAU_DEV]
 
         def job():
             d_phi0.copy_(h_phi0, non_blocking=True)
@@ -326,8 +353,8 @@ def run_ours(args):
         threads = os.cpu_count() or 1
         mlups, secs = cpu_oracle_mlups(args.cpu_n, args.cpu_steps, threads)
         cpu = {"value": mlups, "unit": UNIT, "cores": threads, "kind": "oracle",
-               "sample": "FP64 CPU oracle, D3Q19 %d^3 sample of the workload, %d steps (%.1f s)" % (
-                   args.cpu_n, args.cpu_steps, secs)}
+               "sample": "FP64 CPU oracle, D3Q19 %d^3 sample of the workload, %d steps at each tau in "
+                         "{0.6, 0.8, 1.2} (%.1f s)" % (args.cpu_n, args.cpu_steps, secs)}
 
     if rank == 0:
         line = {"metric": METRIC, "value": fp64["mlups"], "unit": UNIT, "n_gpus": ws, "steps": K,
@@ -335,11 +362,12 @@ def run_ours(args):
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": dict(workload(n), parallelism="replicas" if ws > 1 else "single GPU"),
                 "forms": forms,
-                "roofline": {"bound": "hbm", "kernel": "k_step_fp64<3,fwd,periodic,s=2>",
+                "roofline": {"bound": "hbm", "kernel": "k_step_fp64<3,fwd,periodic,scaled> (tau in {0.6, 0.8, 1.2}; "
+                                                      "1 launch in 49..218 is the renormalising general form)",
                              "achieved": fp64["gbs_per_gpu"], "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                              "frac": fp64["gbs_per_gpu"] / peak, "traffic": traffic,
                              "algorithmic_bytes_per_launch": BYTES_PER_SITE["fp64"] * S},
-                "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 3 * K,
+                "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": (len(order) + 1) * K,
                 "clocks": clk.summary()}
         print(json.dumps(line))
     if ws > 1:
@@ -515,7 +543,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-baseline", type=int, default=1)
     ap.add_argument("--cpu-n", type=int, default=128)
-    ap.add_argument("--cpu-steps", type=int, default=300)
+    ap.add_argument("--cpu-steps", type=int, default=100)
+    ap.add_argument("--ref-n", type=int, default=128)
     ap.add_argument("--error-steps", type=int, default=2000)
     ap.add_argument("--workload", default="d3q19_256",
                     choices=["d3q19_256", "d4q33_dirichlet", "d5q51_fp32dev", "adjoint", "convergence"])

@@ -101,11 +101,18 @@ def test_fp64_d3q19_tau_sweep(tau):
     assert rel(g, o) < FP64_TOL
 
 
-def test_fp64_d3q19_256cubed_full_size():
-    """The benchmark's workload (D3Q19 256^3, 8 modes, tau = 1/2) and launch configuration, a few
-    steps, every node compared."""
-    g, o = run_pair(3, 256, (0.1, 0.1, 0.1), 4, tau=0.5, nmodes=8, seed=2)
-    assert relerr(g, o) < FP64_TOL
+@pytest.mark.parametrize("tau", [0.6, 0.8, 1.2, 0.5])
+def test_fp64_d3q19_256cubed_full_size(tau):
+    """The benchmark's workload (D3Q19 256^3, 8 modes, tau in {0.6, 0.8, 1.2}, plus tau = 1/2) and
+    launch configuration (scaled collision for tau != 1/2), a few steps, every node compared."""
+    g, o = run_pair(3, 256, (0.1, 0.1, 0.1), 4, tau=tau, nmodes=8, seed=2)
+    assert rel(g, o) < FP64_TOL
+
+
+def test_fp32dev_d3q19_256cubed_full_size():
+    """The benchmark's FP32-deviation form (D3Q19 256^3, tau = 0.8), every node compared."""
+    g, o = run_pair(3, 256, (0.1, 0.1, 0.1), 4, tau=0.8, nmodes=8, seed=2, precision="fp32dev")
+    assert rel(g, o) < DEV_TOL
 
 
 def test_fp64_source_field_and_fd_gradient():

@@ -72,6 +72,12 @@ typedef enum { LHE_FP64 = 0, LHE_FP32_DEV = 1 } lhe_precision;
  * LHE_M4_EXPLICIT -- m4[p] for the pairs i<j in lexicographic order, in units of c^4. */
 typedef enum { LHE_M4_RULE = 0, LHE_M4_EXPLICIT = 1 } lhe_m4_mode;
 
+/* lhe_lbm_params.flags. LHE_FLAG_NO_STAGING: run the FP32-deviation step of periodic D3Q19 boxes
+ * with the register-pull kernel instead of the one that stages the pulled rows in shared memory
+ * by bulk asynchronous copies (both compute the same bits; the staged one is the default where
+ * its layout conditions hold: n_1 a multiple of 4 and at most 512). */
+#define LHE_FLAG_NO_STAGING 1
+
 typedef struct {
   int32_t d;              /* spatial dimension, 1..5 */
   int32_t bc;             /* lhe_bc_kind */
@@ -80,7 +86,7 @@ typedef struct {
   int32_t bc_order;       /* full-way: 1, 3 or 4 (Eq. (bun1)); half-way: 1..4 (Eq. (bun2)); unused if periodic */
   int32_t m4_mode;        /* lhe_m4_mode */
   int32_t allow_unstable; /* nonzero: accept weights with omega_k <= 0 (otherwise LHE_ERR_UNSTABLE) */
-  int32_t reserved0;      /* must be 0 */
+  int32_t flags;          /* 0, or LHE_FLAG_* bits (kernel choices; results are identical) */
   int64_t n[LHE_MAX_DIM]; /* nodes per dimension (first d used); full-way n >= 3, otherwise n >= 3 */
   double lo[LHE_MAX_DIM]; /* box [lo, hi] per dimension */
   double hi[LHE_MAX_DIM];

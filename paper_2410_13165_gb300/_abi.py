@@ -21,6 +21,7 @@ STATUS_NAMES = ["LHE_OK", "LHE_ERR_ARG", "LHE_ERR_UNSTABLE", "LHE_ERR_CUDA", "LH
 BC_PERIODIC, BC_FULLWAY, BC_HALFWAY = 0, 1, 2
 FP64, FP32_DEV = 0, 1
 M4_RULE, M4_EXPLICIT = 0, 1
+FLAG_NO_STAGING = 1
 
 # every entry point declared in include/lhe_lbm.h
 EXPORTS = [
@@ -36,7 +37,7 @@ class lhe_lbm_params(ctypes.Structure):
     _fields_ = [
         ("d", ctypes.c_int32), ("bc", ctypes.c_int32), ("precision", ctypes.c_int32),
         ("init_order", ctypes.c_int32), ("bc_order", ctypes.c_int32), ("m4_mode", ctypes.c_int32),
-        ("allow_unstable", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+        ("allow_unstable", ctypes.c_int32), ("flags", ctypes.c_int32),
         ("n", ctypes.c_int64 * MAX_DIM), ("lo", ctypes.c_double * MAX_DIM), ("hi", ctypes.c_double * MAX_DIM),
         ("c", ctypes.c_double), ("u", ctypes.c_double * MAX_DIM), ("R", ctypes.c_double),
         ("tau", ctypes.c_double), ("g", ctypes.c_double), ("m4", ctypes.c_double * 10),

@@ -116,7 +116,7 @@ lhe_status build_model(const lhe_lbm_params *p, Model &m, lhe_lbm *err_to) {
     return fail(err_to, LHE_ERR_ARG, "half-way bc_order must be 1..4");
   if (!(p->c > 0.0) || !std::isfinite(p->c)) return fail(err_to, LHE_ERR_ARG, "c must be positive");
   if (!(p->tau > 0.0) || !std::isfinite(p->tau)) return fail(err_to, LHE_ERR_ARG, "tau must be positive");
-  if (p->reserved0 != 0) return fail(err_to, LHE_ERR_ARG, "reserved0 must be 0");
+  if (p->flags & ~LHE_FLAG_NO_STAGING) return fail(err_to, LHE_ERR_ARG, "unknown bits in flags");
   if (p->m4_mode != LHE_M4_RULE && p->m4_mode != LHE_M4_EXPLICIT) return fail(err_to, LHE_ERR_ARG, "unknown m4_mode");
   if (p->m4_mode == LHE_M4_RULE && !(p->g >= 0.0 && p->g <= 1.0)) return fail(err_to, LHE_ERR_ARG, "g must be in [0, 1]");
   double dxs[kMaxD];
@@ -271,6 +271,14 @@ lhe_status unscale(lhe_lbm *l, int which) {
   return LHE_OK;
 }
 
+// A staged step whose pipeline wait expired stops early and sets a host-mapped flag; the next step
+// call reports it (the state is then incomplete).
+lhe_status check_pipeline(lhe_lbm *l) {
+  if (l->tma_err_host && *(volatile int32_t *)l->tma_err_host)
+    return fail(l, LHE_ERR_CUDA, "a staged step kernel timed out waiting for its copies; the state is invalid");
+  return LHE_OK;
+}
+
 lhe_status check_handle(lhe_lbm *l) {
   if (!l) return fail(nullptr, LHE_ERR_ARG, "handle is NULL");
   return LHE_OK;
@@ -395,6 +403,21 @@ lhe_status lhe_lbm_create(const lhe_lbm_params *p, lhe_lbm **out) {
     e = cudaMalloc(&l->bc_axis, sizeof(double) * 2 * (size_t)kMaxModes * (size_t)sum_n);
     if (e != cudaSuccess) return bail(cuda_fail(l, e, "cudaMalloc(boundary phase table)"));
   }
+  if (p->d == 3 && p->bc == LHE_BC_PERIODIC && p->precision == LHE_FP32_DEV && !(p->flags & LHE_FLAG_NO_STAGING)) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms > 0 && plan_dev3_tma(l->g, sms, l->tma)) {
+      e = cudaHostAlloc((void **)&l->tma_err_host, sizeof(int32_t), cudaHostAllocMapped);
+      if (e != cudaSuccess) return bail(cuda_fail(l, e, "cudaHostAlloc(pipeline flag)"));
+      *l->tma_err_host = 0;
+      e = cudaHostGetDevicePointer((void **)&l->tma.err, l->tma_err_host, 0);
+      if (e != cudaSuccess) return bail(cuda_fail(l, e, "cudaHostGetDevicePointer(pipeline flag)"));
+      e = prepare_dev3_tma(l->tma);
+      if (e != cudaSuccess) return bail(cuda_fail(l, e, "shared-memory size of the staged step"));
+      l->staged = true;
+    }
+  }
   *out = l;
   return LHE_OK;
 }
@@ -415,6 +438,7 @@ lhe_status lhe_lbm_destroy(lhe_lbm *l) {
   cudaFree(l->bc_table);
   cudaFree(l->bc_axis);
   cudaFree(l->red_partials);
+  if (l->tma_err_host) cudaFreeHost(l->tma_err_host);
   delete l;
   return LHE_OK;
 }
@@ -618,6 +642,7 @@ lhe_status lhe_lbm_step(lhe_lbm *l, int64_t n) {
   if (lhe_status s = check_handle(l)) return s;
   if (n < 0) return fail(l, LHE_ERR_ARG, "n must be >= 0");
   if (!l->initialised) return fail(l, LHE_ERR_STATE, "lhe_lbm_step before lhe_lbm_init");
+  if (lhe_status st = check_pipeline(l)) return st;
   const bool periodic = l->p.bc == LHE_BC_PERIODIC;
   if (!periodic && !l->have_wave) return fail(l, LHE_ERR_STATE, "Dirichlet box without boundary data (lhe_lbm_set_boundary_wave)");
   const int d = l->p.d;
@@ -633,8 +658,9 @@ lhe_status lhe_lbm_step(lhe_lbm *l, int64_t n) {
     a.phi_src = l->phi[l->cur];
     a.phi_dst = l->phi[1 - l->cur];
     a.nwork = periodic ? l->g.S : l->g.S_interior;
-    cudaError_t e = dev ? launch_step_dev(d, false, !periodic, a, l->stream)
-                        : launch_step_fp64(d, false, !periodic, a, l->stream);
+    cudaError_t e = l->staged ? launch_step_dev3_tma(false, a, l->tma, l->stream)
+                    : dev         ? launch_step_dev(d, false, !periodic, a, l->stream)
+                                  : launch_step_fp64(d, false, !periodic, a, l->stream);
     if (e != cudaSuccess) return cuda_fail(l, e, "step kernel launch");
     if (!periodic) {
       b.src = a.src;
@@ -750,6 +776,7 @@ lhe_status lhe_lbm_adjoint_step(lhe_lbm *l, int64_t n) {
   if (lhe_status s = check_handle(l)) return s;
   if (n < 0) return fail(l, LHE_ERR_ARG, "n must be >= 0");
   if (!l->adj_ready) return fail(l, LHE_ERR_STATE, "lhe_lbm_adjoint_step before lhe_lbm_adjoint_seed");
+  if (lhe_status st = check_pipeline(l)) return st;
   const bool dev = l->p.precision == LHE_FP32_DEV;
   StepArgs a = step_args(l);
   a.Rfield = nullptr;
@@ -762,8 +789,9 @@ lhe_status lhe_lbm_adjoint_step(lhe_lbm *l, int64_t n) {
     a.dst = l->adj[1 - l->acur];
     a.phi_src = l->adjW[l->acur];
     a.phi_dst = l->adjW[1 - l->acur];
-    cudaError_t e = dev ? launch_step_dev(l->p.d, true, false, a, l->stream)
-                        : launch_step_fp64(l->p.d, true, false, a, l->stream);
+    cudaError_t e = l->staged ? launch_step_dev3_tma(true, a, l->tma, l->stream)
+                    : dev         ? launch_step_dev(l->p.d, true, false, a, l->stream)
+                                  : launch_step_fp64(l->p.d, true, false, a, l->stream);
     if (e != cudaSuccess) return cuda_fail(l, e, "adjoint step kernel launch");
     l->acur ^= 1;
   }

@@ -45,6 +45,23 @@ struct StepArgs {
   int64_t nwork;           // number of sites processed (S, or the interior count)
 };
 
+// Plan of the staged FP32-deviation step on periodic D3Q19 boxes (lhe_step_dev_tma.cu).
+constexpr int kTmaMaxStages = 4;
+struct DevTmaPlan {
+  int32_t nx = 0, ny = 0, nz = 0;
+  int32_t R = 0;           // x-rows per tile (R divides ny)
+  int32_t NS = 0;          // pipeline stages
+  int32_t tiles_y = 0, ntiles = 0, grid = 0;
+  uint32_t g_bytes = 0;    // populations part of a stage: Q * R * nx floats
+  uint32_t phi_bytes = 0;  // 3 (R + 2) nx float2 of phi
+  uint32_t x_bytes = 0;    // R nx doubles: dL/dR (adjoint) or R(x) (forward) of the tile, when used
+  uint32_t stage_bytes = 0;  // g_bytes + phi_bytes + room for x_bytes
+  uint32_t tx_bytes = 0;   // bytes copied per tile in this launch (x part only when used)
+  FastDiv nx_div;
+  int8_t ey[kMaxQ] = {}, ez[kMaxQ] = {};  // y and z components of e_k
+  int32_t *err = nullptr;  // host-mapped flag, set when a pipeline wait timed out
+};
+
 // FP64 collision forms for s != 2.
 constexpr int kCollideGeneral = 0;  // two FP64 operations per population
 constexpr int kCollideScaled = 1;   // scaled representation, one FMA per population
@@ -129,6 +146,9 @@ cudaError_t launch_adjoint_seed(int d, bool dev, const Geom &g, const double *om
                                 void *adj, float2 *adjW, double *gR, cudaStream_t st);
 cudaError_t launch_df_to_double(const float2 *src, double *dst, int64_t n, cudaStream_t st);
 cudaError_t launch_scale_fp64(double *p, int64_t n, double factor, cudaStream_t st);
+bool plan_dev3_tma(const Geom &g, int sms, DevTmaPlan &p);
+cudaError_t prepare_dev3_tma(const DevTmaPlan &p);
+cudaError_t launch_step_dev3_tma(bool adjoint, const StepArgs &a, const DevTmaPlan &p, cudaStream_t st);
 cudaError_t launch_adjoint_grads(int d, bool dev, const AdjGradArgs &a, cudaStream_t st);
 
 // Record the message lhe_lbm_last_error(NULL) returns on this thread; returns `status`.
@@ -173,6 +193,10 @@ struct lhe_lbm {
   // Scaled representation of the FP64 state when s != 2 on periodic boxes: the stored populations
   // are K f* with K = (1 - s)^-j; j = 0 means the state is stored as f* itself. [0] forward, [1]
   // adjoint. acc accumulates the relative error of the rounded s/(1 - s) factors.
+  // staged FP32-deviation step (periodic D3Q19)
+  bool staged = false;
+  lhe::DevTmaPlan tma{};
+  int32_t *tma_err_host = nullptr;
   int32_t scale_j[2] = {0, 0};
   double scale_acc[2] = {0.0, 0.0};
   // diagnostics

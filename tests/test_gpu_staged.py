@@ -1,0 +1,123 @@
+"""GPU: the staged FP32-deviation step (periodic D3Q19, rows brought into shared memory by bulk
+asynchronous copies) against the register-pull kernel, bit for bit, and against the oracle.
+
+Both kernels evaluate the same per-node arithmetic in the same order, so every population, phi and
+dL/dR must agree exactly; the shapes cover tiles of one and several rows, wrap-around in y and z
+on grids of 3 rows, the maximum row length and extents the staged kernel does not take."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2410_13165_gb300 import LBM, build, workloads as W
+from paper_2410_13165_gb300 import _abi
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    build.build()
+    _abi.load()
+
+
+def _t(a):
+    import torch
+
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64).ravel()).cuda()
+
+
+def _problem(n, seed):
+    m = O.Model(3, list(n), 0.0, [ni / 32.0 for ni in n], [0.0] * 3)
+    X = m.coords()
+    F = W.fourier_field(3, 4, seed, 0.0, [ni / 32.0 for ni in n])
+    return F.value(X), F.grad(X)
+
+
+def _pair(n, tau, steps, R=0.0, Rf=None, seed=0):
+    import torch
+
+    phi0, grad = _problem(n, seed)
+    out = []
+    for staged in (True, False):
+        sim = LBM(3, list(n), 0.0, [ni / 32.0 for ni in n], u=(0.1, -0.05, 0.08), tau=tau, R=R,
+                  precision="fp32dev", staged=staged)
+        sim.init(_t(phi0), _t(grad), None if Rf is None else _t(Rf))
+        sim.step(steps)
+        out.append((sim.get_state().clone(), sim.macro().clone()))
+        sim.close()
+    torch.cuda.synchronize()
+    return out, phi0, grad
+
+
+SHAPES = [(16, 12, 8), (32, 6, 5), (12, 20, 7), (64, 8, 3), (8, 3, 4), (128, 4, 3), (512, 3, 3), (4, 5, 6),
+          (20, 9, 5), (10, 6, 4), (576, 3, 3)]
+
+
+@pytest.mark.parametrize("n", SHAPES)
+@pytest.mark.parametrize("tau", [0.5, 0.8])
+def test_staged_step_is_bitwise_the_register_kernel(n, tau):
+    import torch
+
+    (st_a, phi_a), (st_b, phi_b) = _pair(n, tau, 13, seed=sum(n))[0]
+    assert torch.equal(st_a, st_b)
+    assert torch.equal(phi_a, phi_b)
+
+
+def test_staged_step_with_sources_matches_the_oracle():
+    import torch
+
+    n = (32, 12, 6)
+    S = int(np.prod(n))
+    Rf = 0.4 * np.sin(np.arange(S) * 0.013)
+    (res, phi0, grad) = _pair(n, 0.8, 40, Rf=Rf, seed=3)
+    (st_a, phi_a), (st_b, phi_b) = res
+    assert torch.equal(st_a, st_b) and torch.equal(phi_a, phi_b)
+    m = O.Model(3, list(n), 0.0, [ni / 32.0 for ni in n], (0.1, -0.05, 0.08), tau=0.8)
+    o = m.phi(m.step(m.init(phi0, grad, 3), 0, 40, Rfield=Rf))
+    g = phi_a.cpu().numpy()
+    assert np.max(np.abs(g - o)) < 1e-5 * max(np.max(np.abs(o)), np.max(np.abs(phi0)))
+    (res, _, _) = _pair(n, 0.5, 40, R=2.5, seed=4)
+    assert torch.equal(res[0][0], res[1][0])
+
+
+@pytest.mark.parametrize("tau", [0.5, 1.2])
+def test_staged_adjoint_is_bitwise_the_register_kernel(tau):
+    import torch
+
+    n = (32, 8, 6)
+    phi0, grad = _problem(n, 9)
+    rng = np.random.default_rng(10)
+    target = rng.normal(size=int(np.prod(n)))
+    res = []
+    for staged in (True, False):
+        sim = LBM(3, list(n), 0.0, [ni / 32.0 for ni in n], u=(0.1, -0.05, 0.08), tau=tau, precision="fp32dev",
+                  staged=staged)
+        sim.init(_t(phi0), _t(grad), _t(0.1 * target))
+        sim.step(20)
+        r = sim.macro() - _t(target)
+        sim.adjoint_seed(r.contiguous())
+        sim.adjoint_step(20)
+        gphi, ggrad, gR = sim.adjoint_grads(want_grad=True, want_R=True)
+        res.append((gphi.clone(), ggrad.clone(), gR.clone()))
+        sim.close()
+    for a, b in zip(*res):
+        assert torch.equal(a, b)
+
+
+def test_staged_step_full_size_256():
+    """The benchmark's FP32-deviation workload and launch configuration (D3Q19 256^3, tau = 0.8)."""
+    import torch
+
+    n = 256
+    phi0, grad, _, _ = W.periodic_problem(3, n, 8, 2)
+    res = []
+    for staged in (True, False):
+        sim = LBM(3, n, u=(0.1, 0.1, 0.1), tau=0.8, precision="fp32dev", staged=staged)
+        sim.init(_t(phi0), _t(grad))
+        sim.step(3)
+        res.append(sim.get_state().clone())
+        sim.close()
+    assert torch.equal(res[0], res[1])

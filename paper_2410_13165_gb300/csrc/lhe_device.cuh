@@ -161,6 +161,20 @@ __device__ __forceinline__ float2 df_split(double x) {
   return make_float2((float)hd, (float)(x - hd));
 }
 
+// New pair for h + t, with h the leading part of a pair and t an FP32 increment: h' is the exact sum
+// rounded toward zero to 24 significant bits, l' = (h + t) - h' rounded to nearest. TwoSum gives
+// s + e = h + t exactly (s the rounded-to-nearest sum); when s was rounded away from zero it is moved
+// one step toward zero, and s - h' (0 or one ulp) is exact. FP32 arithmetic only (the intrinsics
+// keep the compiler from contracting or reordering the error terms).
+__device__ __forceinline__ float2 df_add(float h, float t) {
+  const float s = __fadd_rn(h, t);
+  const float bp = __fsub_rn(s, h);
+  const float e = __fadd_rn(__fsub_rn(h, __fsub_rn(s, bp)), __fsub_rn(t, bp));
+  const bool away = (s > 0.0f && e < 0.0f) || (s < 0.0f && e > 0.0f);
+  const float hn = away ? __int_as_float(__float_as_int(s) - 1) : s;
+  return make_float2(hn, __fadd_rn(__fsub_rn(s, hn), e));
+}
+
 // Streaming stores: the new state is not re-read by this kernel.
 __device__ __forceinline__ void st_stream(double *p, double v) { __stcs(p, v); }
 __device__ __forceinline__ void st_stream(float *p, float v) { __stcs(p, v); }

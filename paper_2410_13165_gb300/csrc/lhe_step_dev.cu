@@ -10,7 +10,8 @@
 //   g*_k(new)   = (1 - s) g_k + dt omega_k R(x)                 (Eq. (BGK-LB-Evolution))
 // Delta and the deviations are O(dx) and carried in FP32; the neighbour differences are
 // delta_k = (h_k - h) + (l_k - l) in FP32 (exact leading part by Sterbenz for nearby values), and
-// the moment update phi_new = h + (l + Delta) is accumulated in FP64 and re-split.
+// the moment update phi_new = h + (l + Delta) is formed as an exact FP32 pair (df_add: TwoSum,
+// leading part the exact sum truncated to 24 bits, residual rounded to nearest).
 //
 // The adjoint uses the same kernel with the reverse pull (x + e_k), no source, and the weighted
 // adjoint variable zeta_k = omega_k W + eps_k (W a double-float pair, eps in FP32); W_new is
@@ -52,9 +53,9 @@ __global__ void __launch_bounds__(LHE_STEP_THREADS) k_step_dev(const StepArgs a)
     accg += gk[k];
   }
   const float Delta = accw + accg;
-  const double phin = (double)p0.x + (double)(p0.y + Delta);
-  a.phi_dst[site] = df_split(phin);
-  if (ADJ && a.gR) a.gR[site] = fma(a.dt, phin, a.gR[site]);
+  const float2 pn = df_add(p0.x, p0.y + Delta);
+  a.phi_dst[site] = pn;
+  if (ADJ && a.gR) a.gR[site] = fma(a.dt, df_value(pn), a.gR[site]);
   float dtR = 0.0f;
   const bool field = !ADJ && a.Rfield != nullptr;
   if (field) dtR = (float)(a.dt * __ldg(a.Rfield + site));

@@ -243,9 +243,9 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_step_dev3_tma(const StepArgs
         accg += gk[k];
       }
       const float Delta = accw + accg;
-      const double phin = (double)p0.x + (double)(p0.y + Delta);
-      a.phi_dst[site] = df_split(phin);
-      if (ADJ && a.gR) a.gR[site] = fma(a.dt, phin, X[idx]);
+      const float2 pn = df_add(p0.x, p0.y + Delta);
+      a.phi_dst[site] = pn;
+      if (ADJ && a.gR) a.gR[site] = fma(a.dt, df_value(pn), X[idx]);
       float dtR = 0.0f;
       if (field) dtR = (float)(a.dt * X[idx]);
 #pragma unroll

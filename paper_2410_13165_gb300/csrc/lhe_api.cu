@@ -166,6 +166,7 @@ Geom make_geom(int d, const int64_t *n) {
   }
   g.S = stride;
   g.S_interior = si;
+  g.S_rows = d > 1 ? si / (n[0] - 2) * n[0] : n[0];
   return g;
 }
 
@@ -657,7 +658,7 @@ lhe_status lhe_lbm_step(lhe_lbm *l, int64_t n) {
     a.dst = l->pop[1 - l->cur];
     a.phi_src = l->phi[l->cur];
     a.phi_dst = l->phi[1 - l->cur];
-    a.nwork = periodic ? l->g.S : l->g.S_interior;
+    a.nwork = periodic ? l->g.S : l->g.S_rows;
     cudaError_t e = l->staged ? launch_step_dev3_tma(false, a, l->tma, l->stream)
                     : dev         ? launch_step_dev(d, false, !periodic, a, l->stream)
                                   : launch_step_fp64(d, false, !periodic, a, l->stream);

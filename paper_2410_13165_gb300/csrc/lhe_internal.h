@@ -17,9 +17,10 @@ struct Geom {
   int32_t n[kMaxD] = {1, 1, 1, 1, 1};
   int32_t stride[kMaxD] = {0, 0, 0, 0, 0};
   FastDiv dv[kMaxD];   // divide by n_i (site -> coordinates)
-  FastDiv dvi[kMaxD];  // divide by n_i - 2 (interior index -> coordinates)
+  FastDiv dvi[kMaxD];  // divide by n_i - 2 (interior row index -> coordinates)
   int64_t S = 0;
   int64_t S_interior = 0;
+  int64_t S_rows = 0;  // n_1 * prod_{i>1} (n_i - 2): the whole x-rows through interior nodes
 };
 
 // Arguments of the fused stream + collide kernels (forward and adjoint, both precisions).

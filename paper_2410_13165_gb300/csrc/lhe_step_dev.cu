@@ -29,6 +29,7 @@ __global__ void __launch_bounds__(LHE_STEP_THREADS) k_step_dev(const StepArgs a)
   if (t >= a.nwork) return;
   int x[D];
   const int32_t site = decode_site<D, INTERIOR>(a.g, t, x);
+  if (skip_site<D, INTERIOR>(a.g, x)) return;
   int32_t om[D], op[D];
   axis_offsets<D, INTERIOR>(a.g, x, om, op);
   const float *__restrict__ src = static_cast<const float *>(a.src);

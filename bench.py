@@ -533,6 +533,45 @@ def run_convergence(args):
     return 0
 
 
+def run_order_law(args):
+    """Eq. (cr-estimation) on the GPU: convergence rates of the Dirichlet schemes against the boundary
+    order P and the initialisation order K (2D, Example 1's setting with R = 5 and exact solutions of
+    the wave family, T = 2; full-way at u = (0.1, 0.1), half-way at u = (0.01, 0.01); N = 20, 40, 80)."""
+    import torch
+
+    from paper_2410_13165_gb300 import LBM, build
+    from paper_2410_13165_gb300 import workloads as W
+
+    build.build()
+    wave = dict(a=[1.0, 0.5], kappa=[(np.pi, np.pi), (2.0, -1.0)], theta=[0.3, 1.1], b=0.2)
+
+    def rmse(bc, P, K, N, u):
+        n = N + 1 if bc == "fullway" else N
+        X = W.node_coords(2, n, 0.0, 1.0 / N, halfway=(bc == "halfway"))
+        phi0, grad = W.wave_solution(X, 0.0, u, 5.0, **wave)
+        sim = LBM(2, n, u=u, R=5.0, bc=bc, bc_order=P, init_order=K)
+        sim.init(torch.from_numpy(phi0).cuda(), torch.from_numpy(np.ascontiguousarray(grad).ravel()).cuda())
+        sim.set_boundary_wave(wave["a"], wave["kappa"], wave["theta"], wave["b"])
+        steps = int(round(2.0 / sim.dt))
+        sim.step(steps)
+        ex, _ = W.wave_solution(X, steps * sim.dt, u, 5.0, **wave)
+        e = float(np.sqrt(np.mean((sim.macro().cpu().numpy() - ex) ** 2)))
+        sim.close()
+        return e
+
+    out = {"metric": "convergence rate vs boundary order P and init order K (Eq. (cr-estimation))", "unit": "rate",
+           "grids": [20, 40, 80]}
+    for bc, u, Ps in (("fullway", (0.1, 0.1), (1, 3, 4)), ("halfway", (0.01, 0.01), (1, 2, 3, 4))):
+        for P in Ps:
+            for K in (1, 3):
+                errs = [rmse(bc, P, K, N, u) for N in (20, 40, 80)]
+                out["%s_P%d_K%d" % (bc, P, K)] = {
+                    "rmse": errs, "rates": [float(np.log2(a / b)) for a, b in zip(errs, errs[1:])],
+                    "law_min_K+1_P": min(K + 1, P)}
+    print(json.dumps(out))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -547,12 +586,13 @@ def main():
     ap.add_argument("--ref-n", type=int, default=128)
     ap.add_argument("--error-steps", type=int, default=2000)
     ap.add_argument("--workload", default="d3q19_256",
-                    choices=["d3q19_256", "d4q33_dirichlet", "d5q51_fp32dev", "adjoint", "convergence"])
+                    choices=["d3q19_256", "d4q33_dirichlet", "d5q51_fp32dev", "adjoint", "convergence",
+                             "order_law"])
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
     others = {"d4q33_dirichlet": run_d4q33_dirichlet, "d5q51_fp32dev": run_d5q51_fp32dev,
-              "adjoint": run_adjoint_ratio, "convergence": run_convergence}
+              "adjoint": run_adjoint_ratio, "convergence": run_convergence, "order_law": run_order_law}
     if args.workload in others:
         if args.steps == 400:
             args.steps = 50

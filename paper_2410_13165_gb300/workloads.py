@@ -104,3 +104,20 @@ def periodic_problem(d: int, n: int, nmodes: int, seed: int, lo=0.0, hi=1.0):
     X = node_coords(d, n, lo, dx)
     F = fourier_field(d, nmodes, seed, lo, hi)
     return F.value(X), F.grad(X), F, X
+
+
+def wave_solution(X: np.ndarray, t: float, u, R: float, a, kappa, theta, b: float = 0.0, g=None):
+    """Value and gradient of h = b + R t + g.(x - u t) + sum_m a_m sin(kappa_m.(x - u t) + theta_m) at the
+    (d, S) coordinates X: an exact solution of d_t h + u.grad h = R (the Dirichlet data family of the
+    library); used to build initial data and to measure errors."""
+    d = X.shape[0]
+    Y = X - np.asarray(u, dtype=np.float64)[:, None] * t
+    gv = np.zeros(d) if g is None else np.asarray(g, dtype=np.float64)
+    val = b + R * t + gv @ Y
+    grad = np.repeat(gv[:, None], X.shape[1], axis=1)
+    for am, km, tm in zip(a, kappa, theta):
+        km = np.asarray(km, dtype=np.float64)
+        arg = km @ Y + tm
+        val = val + am * np.sin(arg)
+        grad = grad + am * km[:, None] * np.cos(arg)[None, :]
+    return val, grad

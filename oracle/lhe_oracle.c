@@ -455,12 +455,28 @@ double orc_entropy(const orc_model *m, const double *f) {
   return acc;
 }
 
-/* ------------------------------------------------------------------ adjoint (periodic) */
+/* ------------------------------------------------------------------ adjoint */
 
-/* Transpose of orc_step for a periodic box. With lam_next = dL/df(t_{n+1}):
- *   mu_k(x) = dL/df*_k(x) = lam_next_k(x + e_k)         (transpose of the push)
+static int opposite_link(const orc_model *m, int k) {
+  for (int j = 0; j < m->Q; ++j) {
+    int same = 1;
+    for (int i = 0; i < m->d; ++i)
+      if (m->e[j * m->d + i] != -m->e[k * m->d + i]) same = 0;
+    if (same) return j;
+  }
+  return -1;
+}
+
+/* Transpose of orc_step. With lam_next = dL/df(t_{n+1}) (pre-collision populations):
+ *   mu_k(x) = dL/df*_k(x). The push sends f*_k(x) to x + e_k, so mu_k(x) = lam_next_k(x + e_k)
+ *             when that node exists (periodic: always, with wrap). On a Dirichlet box a link that
+ *             leaves the box feeds nothing in the full-way scheme (Eq. (bun1): the unknown
+ *             population at the far side is set from the boundary data alone), while in the
+ *             half-way scheme the unknown population of the opposite link at the same node is
+ *             f_kbar(x) = -f*_k(x) + B (Eq. (bun2)), so mu_k(x) = -lam_next_kbar(x).
  *   gR(x)  += dt sum_k omega_k mu_k(x)                  (f*_k carries dt omega_k R(x))
- *   lam_j(x) = sum_k mu_k(x) (d f*_k / d f_j) = (1 - s) mu_j + s sum_k omega_k mu_k. */
+ *   lam_j(x) = (1 - s) mu_j(x) + s sum_k omega_k mu_k(x)   (collision f* = f - s(f - omega phi))
+ * The boundary data enter the step additively, so they do not appear in the transpose. */
 void orc_adjoint_step(const orc_model *m, const double *lam_next, double *lam, double *gR) {
   const int d = m->d, Q = m->Q;
   const int64_t S = n_sites(m);
@@ -471,8 +487,15 @@ void orc_adjoint_step(const orc_model *m, const double *lam_next, double *lam, d
     site_to_idx(m, site, idx);
     double wmu = 0.0;
     for (int k = 0; k < Q; ++k) {
-      for (int i = 0; i < d; ++i) dst[i] = ((idx[i] + m->e[k * d + i]) % m->n[i] + m->n[i]) % m->n[i];
-      mu[k] = lam_next[(int64_t)k * S + idx_to_site(m, dst)];
+      int inside = 1;
+      for (int i = 0; i < d; ++i) {
+        dst[i] = idx[i] + m->e[k * d + i];
+        if (m->bc == 0) dst[i] = (dst[i] + m->n[i]) % m->n[i];
+        else if (dst[i] < 0 || dst[i] >= m->n[i]) inside = 0;
+      }
+      if (inside) mu[k] = lam_next[(int64_t)k * S + idx_to_site(m, dst)];
+      else if (m->bc == 2) mu[k] = -lam_next[(int64_t)opposite_link(m, k) * S + site];
+      else mu[k] = 0.0;
       wmu += m->omega[k] * mu[k];
     }
     if (gR) gR[site] += m->dt * wmu;
@@ -488,6 +511,7 @@ void orc_adjoint_init(const orc_model *m, int order, int grad_is_fd, const doubl
   const int d = m->d, Q = m->Q;
   const int64_t S = n_sites(m);
   const double c = m->dx / m->dt;
+  if (S <= 0) return;
   double *G = NULL;
   if (order == 3) G = (double *)calloc((size_t)d * (size_t)S, sizeof(double));
   for (int64_t site = 0; site < S; ++site) {

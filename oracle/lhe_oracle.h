@@ -77,7 +77,7 @@ void orc_exact_grad_field(const orc_model *m, const orc_wave *w, double t, doubl
 /* ---- diagnostics ---- */
 double orc_entropy(const orc_model *m, const double *f); /* sum_x sum_k f_k^2/(2 omega_k), Eq. (skfk) */
 
-/* ---- discrete adjoint of the periodic scheme ---- */
+/* ---- discrete adjoint (periodic and Dirichlet boxes; see orc_adjoint_step) ---- */
 void orc_adjoint_step(const orc_model *m, const double *lam_next, double *lam, double *gR);
 void orc_adjoint_init(const orc_model *m, int order, int grad_is_fd, const double *lam0,
                       double *gphi0, double *ggrad);

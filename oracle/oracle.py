@@ -282,7 +282,7 @@ class Model:
     def entropy(self, f) -> float:
         return lib().orc_entropy(ctypes.byref(self._m), _p(np.ascontiguousarray(f)))
 
-    # adjoint (periodic)
+    # adjoint (periodic and Dirichlet boxes)
     def adjoint_step(self, lam_next, gR=None) -> np.ndarray:
         lam = np.empty_like(lam_next)
         lib().orc_adjoint_step(ctypes.byref(self._m), _p(np.ascontiguousarray(lam_next)), _p(lam), _p(gR))
@@ -295,14 +295,18 @@ class Model:
                                _p(np.ascontiguousarray(lam0)), _p(gphi), _p(ggrad))
         return gphi, ggrad
 
-    def gradient(self, phi0, Rfield, target, T, order=3, grad=None):
+    def gradient(self, phi0, Rfield, target, T, order=3, grad=None, wave=None):
         """Loss L = 1/2 sum_x (phi(T) - target)^2 and its exact discrete gradients w.r.t. phi0,
-        the source field R(x) and (when grad is given) grad phi0. Stores every state (tiny grids)."""
+        the source field R(x) and (when grad is given) grad phi0. Dirichlet boxes take their
+        boundary data (wave) and an explicit grad phi0; the R gradient is then that of the
+        collision source only. Stores every state (tiny grids)."""
         grad_is_fd = grad is None
+        if self.bc != "periodic" and grad_is_fd:
+            raise ValueError("Dirichlet boxes need an explicit grad phi0")
         f = self.init(phi0, grad, order)
         states = [f]
         for n in range(T):
-            f = self.step(f, n0=n, nsteps=1, Rfield=Rfield)
+            f = self.step(f, n0=n, nsteps=1, wave=wave, Rfield=Rfield)
             states.append(f)
         phiT = self.phi(f)
         r = phiT - np.asarray(target).reshape(self.S)

@@ -93,3 +93,79 @@ def test_gradient_dense_jacobian_on_a_tiny_grid():
     _, gphi0, gR, _ = m.gradient(phi0, R, target, T)
     assert np.max(np.abs(gphi0 - J0.T @ res)) < 1e-12
     assert np.max(np.abs(gR - JR.T @ res)) < 1e-12
+
+
+# ---------------------------------------------------------------- Dirichlet boxes
+
+def _dmodel(bc, d=2, n=5, tau=0.5, order=4):
+    u = {2: (0.1, -0.2), 3: (0.1, 0.05, -0.15)}[d]
+    return O.Model(d, n, 0.0, 1.0, u, tau=tau, R=0.7, bc=bc, bc_order=order)
+
+
+def _dwave(m):
+    if m.d == 2:
+        return m.wave(a=[1.0, 0.5], kappa=[(np.pi, np.pi), (2.0, -1.0)], theta=[0.3, 1.1], b=0.2)
+    return m.wave(a=[0.8], kappa=[(np.pi, 1.0, -2.0)], theta=[0.4], b=-0.1)
+
+
+@pytest.mark.parametrize("tau", [0.5, 0.8])
+@pytest.mark.parametrize("bc,d,n", [("fullway", 2, 5), ("halfway", 2, 5), ("fullway", 3, 4), ("halfway", 3, 4)])
+def test_dirichlet_adjoint_step_is_the_transpose(bc, d, n, tau):
+    """The Dirichlet step is affine in the state (the boundary data enter additively): its linear
+    part step(x) - step(0) and the adjoint step are transposes."""
+    m = _dmodel(bc, d, n, tau)
+    w = _dwave(m)
+    rng = np.random.default_rng(60 + d)
+    x = rng.normal(size=(m.Q, m.S))
+    y = rng.normal(size=(m.Q, m.S))
+    zero = np.zeros_like(x)
+    lin = m.step(x, 0, 1, wave=w) - m.step(zero, 0, 1, wave=w)
+    lhs = np.vdot(lin, y)
+    rhs = np.vdot(x, m.adjoint_step(y))
+    assert abs(lhs - rhs) < 1e-12 * max(1.0, abs(lhs))
+
+
+@pytest.mark.parametrize("bc", ["fullway", "halfway"])
+def test_dirichlet_dense_step_matrix_transpose(bc):
+    m = _dmodel(bc, 2, 3)
+    w = _dwave(m)
+    N = m.Q * m.S
+    base = m.step(np.zeros((m.Q, m.S)), 0, 1, wave=w).ravel()
+    A = np.zeros((N, N))
+    B = np.zeros((N, N))
+    for j in range(N):
+        v = np.zeros(N)
+        v[j] = 1.0
+        A[:, j] = m.step(v.reshape(m.Q, m.S), 0, 1, wave=w).ravel() - base
+        B[:, j] = m.adjoint_step(v.reshape(m.Q, m.S)).ravel()
+    assert np.max(np.abs(A.T - B)) < 1e-14
+    if bc == "halfway":  # the -f*_kbar coupling makes some columns feed two entries at one node
+        assert np.count_nonzero(np.abs(A) > 0) > 0
+
+
+def _dloss(m, w, phi0, grad, target, T, order=3):
+    f = m.init(phi0, grad, order)
+    f = m.step(f, 0, T, wave=w)
+    r = m.phi(f) - target
+    return 0.5 * float(r @ r)
+
+
+@pytest.mark.parametrize("bc", ["fullway", "halfway"])
+@pytest.mark.parametrize("tau", [0.5, 0.8])
+def test_dirichlet_gradient_matches_central_differences(bc, tau):
+    m = _dmodel(bc, 2, 6, tau)
+    w = _dwave(m)
+    rng = np.random.default_rng(71)
+    phi0 = rng.normal(size=m.S)
+    grad = rng.normal(size=(2, m.S))
+    target = rng.normal(size=m.S)
+    T = 9
+    loss, gphi0, _, ggrad = m.gradient(phi0, None, target, T, order=3, grad=grad, wave=w)
+    assert abs(loss - _dloss(m, w, phi0, grad, target, T)) < 1e-12 * loss
+    for trial in range(4):
+        vp, vg = rng.normal(size=m.S), rng.normal(size=(2, m.S))
+        h = 10.0 ** (-1 - trial)
+        fd = (_dloss(m, w, phi0 + h * vp, grad + h * vg, target, T) -
+              _dloss(m, w, phi0 - h * vp, grad - h * vg, target, T)) / (2 * h)
+        an = gphi0 @ vp + float(np.sum(ggrad * vg))
+        assert abs(fd - an) < 1e-9 * max(1.0, abs(an)), (fd, an, h)

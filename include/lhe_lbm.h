@@ -212,18 +212,22 @@ LHE_API lhe_status lhe_lbm_diagnostics_noalloc(const lhe_lbm_params *p, const do
 LHE_API lhe_status lhe_lbm_get_state(lhe_lbm *lbm, void *buf);
 LHE_API lhe_status lhe_lbm_set_state(lhe_lbm *lbm, const void *buf, int64_t step);
 
-/* ---------------- discrete adjoint (periodic boxes) ----------------
+/* ---------------- discrete adjoint ----------------
  * The scheme is affine in the populations, so its adjoint needs no forward state: given the
  * cotangent dL/dphi(t_T) of any loss L of the final field, lhe_lbm_adjoint_seed() sets the
  * adjoint state, each lhe_lbm_adjoint_step() applies the transpose of one step (reverse stream,
  * transposed collision) and accumulates dL/dR(x), and lhe_lbm_adjoint_grads() applies the
  * transpose of the initialisation. The adjoint uses the handle's precision and allocates its own
- * buffers on first use. */
+ * buffers on first use. Dirichlet boxes (FP64 only; LHE_ERR_STATE for FP32_DEV): the transpose of
+ * the boundary schemes drops the populations that leave the box (full-way, Eq. (bun1)) or returns
+ * them, negated, to the opposite link of the same node (half-way, Eq. (bun2)); the boundary data
+ * enter additively and have no adjoint here, and dL/dR(x) is not available (constant R). */
 LHE_API lhe_status lhe_lbm_adjoint_seed(lhe_lbm *lbm, const double *dL_dphiT_dev);
 LHE_API lhe_status lhe_lbm_adjoint_step(lhe_lbm *lbm, int64_t n);
 /* dL/dphi0 (S doubles), dL/d(grad phi0) (d*S doubles, only meaningful when lhe_lbm_init got an
- * explicit gradient; NULL to skip), dL/dR(x) (S doubles, NULL to skip). When init used the
- * finite-difference gradient, its transpose is folded into dL/dphi0. */
+ * explicit gradient; NULL to skip), dL/dR(x) (S doubles, NULL to skip; must be NULL on Dirichlet
+ * boxes, else LHE_ERR_ARG). When init used the finite-difference gradient, its transpose is folded
+ * into dL/dphi0. */
 LHE_API lhe_status lhe_lbm_adjoint_grads(lhe_lbm *lbm, double *dL_dphi0_dev, double *dL_dgrad_dev, double *dL_dR_dev);
 
 #ifdef __cplusplus

@@ -511,7 +511,7 @@ void orc_adjoint_init(const orc_model *m, int order, int grad_is_fd, const doubl
   const int d = m->d, Q = m->Q;
   const int64_t S = n_sites(m);
   const double c = m->dx / m->dt;
-  if (S <= 0) return;
+  if (S <= 0 || d <= 0) return;
   double *G = NULL;
   if (order == 3) G = (double *)calloc((size_t)d * (size_t)S, sizeof(double));
   for (int64_t site = 0; site < S; ++site) {

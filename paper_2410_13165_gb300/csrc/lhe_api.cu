@@ -616,7 +616,15 @@ static BoundaryArgs boundary_args(const lhe_lbm *l) {
     off += (int32_t)l->p.n[i];
   }
   b.axis_len = off;
-  for (int k = 0; k < l->Q; ++k) b.omega[k] = l->omega[k];
+  for (int k = 0; k < l->Q; ++k) {
+    b.omega[k] = l->omega[k];
+    for (int j = 0; j < l->Q; ++j) {
+      bool opp = true;
+      for (int i = 0; i < l->p.d; ++i)
+        if (l->e[j * l->p.d + i] != -l->e[k * l->p.d + i]) opp = false;
+      if (opp) b.wratio[k] = l->omega[k] / l->omega[j];
+    }
+  }
   b.s = l->s;
   b.oms = 1.0 - l->s;
   b.R = l->R;
@@ -754,7 +762,8 @@ lhe_status lhe_lbm_set_state(lhe_lbm *l, const void *buf, int64_t step) {
 lhe_status lhe_lbm_adjoint_seed(lhe_lbm *l, const double *seed) {
   if (lhe_status s = check_handle(l)) return s;
   if (!seed) return fail(l, LHE_ERR_ARG, "dL/dphi_T is NULL");
-  if (l->p.bc != LHE_BC_PERIODIC) return fail(l, LHE_ERR_STATE, "the adjoint is implemented for periodic boxes");
+  if (l->p.bc != LHE_BC_PERIODIC && l->p.precision == LHE_FP32_DEV)
+    return fail(l, LHE_ERR_STATE, "the adjoint of a Dirichlet box is implemented for FP64 populations");
   if (!l->initialised) return fail(l, LHE_ERR_STATE, "lhe_lbm_adjoint_seed before lhe_lbm_init");
   const bool dev = l->p.precision == LHE_FP32_DEV;
   const size_t S = (size_t)l->g.S;
@@ -780,9 +789,12 @@ lhe_status lhe_lbm_adjoint_step(lhe_lbm *l, int64_t n) {
   if (lhe_status st = check_pipeline(l)) return st;
   const bool dev = l->p.precision == LHE_FP32_DEV;
   StepArgs a = step_args(l);
+  const bool periodic = l->p.bc == LHE_BC_PERIODIC;
   a.Rfield = nullptr;
-  a.gR = l->gR;
-  a.nwork = l->g.S;
+  a.gR = periodic ? l->gR : nullptr;  // Dirichlet boxes: constant R only, no dL/dR(x)
+  a.nwork = periodic ? l->g.S : l->g.S_rows;
+  BoundaryArgs b{};
+  if (!periodic) b = boundary_args(l);
   const bool scaled = scaled_eligible(l);
   for (int64_t it = 0; it < n; ++it) {
     if (scaled) plan_scaled_step(l, 1, a);
@@ -791,9 +803,15 @@ lhe_status lhe_lbm_adjoint_step(lhe_lbm *l, int64_t n) {
     a.phi_src = l->adjW[l->acur];
     a.phi_dst = l->adjW[1 - l->acur];
     cudaError_t e = l->staged ? launch_step_dev3_tma(true, a, l->tma, l->stream)
-                    : dev         ? launch_step_dev(l->p.d, true, false, a, l->stream)
-                                  : launch_step_fp64(l->p.d, true, false, a, l->stream);
+                    : dev         ? launch_step_dev(l->p.d, true, !periodic, a, l->stream)
+                                  : launch_step_fp64(l->p.d, true, !periodic, a, l->stream);
     if (e != cudaSuccess) return cuda_fail(l, e, "adjoint step kernel launch");
+    if (!periodic) {
+      b.src = a.src;
+      b.dst = a.dst;
+      e = launch_adjoint_boundary(l->p.d, l->p.bc, b, l->stream);
+      if (e != cudaSuccess) return cuda_fail(l, e, "adjoint boundary kernel launch");
+    }
     l->acur ^= 1;
   }
   return LHE_OK;
@@ -803,6 +821,8 @@ lhe_status lhe_lbm_adjoint_grads(lhe_lbm *l, double *gphi0, double *ggrad, doubl
   if (lhe_status s = check_handle(l)) return s;
   if (!l->adj_ready) return fail(l, LHE_ERR_STATE, "lhe_lbm_adjoint_grads before lhe_lbm_adjoint_seed");
   if (!gphi0) return fail(l, LHE_ERR_ARG, "dL/dphi0 is NULL");
+  if (gR && l->p.bc != LHE_BC_PERIODIC)
+    return fail(l, LHE_ERR_ARG, "dL/dR(x) is not available on Dirichlet boxes (their source is a constant R)");
   if (lhe_status st = unscale(l, 1)) return st;
   const bool dev = l->p.precision == LHE_FP32_DEV;
   const int d = l->p.d;

@@ -132,6 +132,85 @@ __global__ void __launch_bounds__(128) k_boundary(const BoundaryArgs a) {
   }
 }
 
+// Adjoint of a Dirichlet step at the boundary nodes (FP64), in the weighted variable
+// rho_k(x) = omega_k dL/df_k(x) of the pre-collision populations (the interior nodes use the bulk
+// adjoint kernel). Transposing the pull: mu_j(x) = omega_j dL/df*_j(x) = rho_j(x + e_j) where
+// x + e_j is a node of the box. Where it is not, the post-collision population leaves the box: in
+// the full-way scheme it feeds nothing (Eq. (bun1) sets the unknown population at the far side
+// from the boundary data alone), in the half-way scheme it is the -f*_j(x) of the unknown
+// f_jbar(x) = -f*_j(x) + B (Eq. (bun2)), so mu_j(x) = -(omega_j / omega_jbar) rho_jbar(x). Then
+// rho_k <- (1 - s) mu_k + s omega_k sum_j mu_j, as in the bulk.
+template <int D, int KIND>
+__global__ void __launch_bounds__(128) k_adj_boundary(const BoundaryArgs a) {
+  constexpr Lattice<D> L{};
+  constexpr int Q = Lattice<D>::Q;
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= a.nsites) return;
+  const int32_t site = a.sites[t];
+  const int64_t S = a.g.S;
+  int x[D];
+  {
+    uint32_t r = (uint32_t)site;
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      if (i == D - 1) {
+        x[i] = (int)r;
+      } else {
+        const uint32_t q = a.g.dv[i].div(r);
+        x[i] = (int)(r - q * (uint32_t)a.g.n[i]);
+        r = q;
+      }
+    }
+  }
+  const double *__restrict__ src = static_cast<const double *>(a.src);
+  double mu[Q];
+#pragma unroll
+  for (int k = 0; k < Q; ++k) {
+    bool inside = true;
+    int32_t o = site;
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      if (L.e[k][i] != 0) {
+        const int xs = x[i] + L.e[k][i];
+        if (xs < 0 || xs >= a.g.n[i]) inside = false;
+        o += L.e[k][i] * a.g.stride[i];
+      }
+    }
+    if (inside) mu[k] = src[k * S + o];
+    else mu[k] = KIND == 2 ? -a.wratio[k] * src[L.opp[k] * S + site] : 0.0;
+  }
+  double *__restrict__ dst = static_cast<double *>(a.dst);
+  if (a.s == 2.0) {
+    const double psi = fixed_moment_sum<Q, 1>(mu);  // 2 sum_j mu_j
+#pragma unroll
+    for (int k = 0; k < Q; ++k) dst[k * S + site] = fma(a.omega[k], psi, -mu[k]);
+  } else {
+    const double psi = a.s * fixed_moment_sum<Q, 0>(mu);
+#pragma unroll
+    for (int k = 0; k < Q; ++k) dst[k * S + site] = fma(a.omega[k], psi, a.oms * mu[k]);
+  }
+}
+
+template <int D>
+static cudaError_t adj_boundary_d(int kind, const BoundaryArgs &a, cudaStream_t st) {
+  if (a.nsites <= 0) return cudaSuccess;
+  const unsigned blocks = (unsigned)((a.nsites + 127) / 128);
+  if (kind == 1) k_adj_boundary<D, 1><<<blocks, 128, 0, st>>>(a);
+  else k_adj_boundary<D, 2><<<blocks, 128, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_boundary(int d, int kind, const BoundaryArgs &a, cudaStream_t st) {
+  switch (d) {
+    case 1: return adj_boundary_d<1>(kind, a, st);
+    case 2: return adj_boundary_d<2>(kind, a, st);
+    case 3: return adj_boundary_d<3>(kind, a, st);
+    case 4: return adj_boundary_d<4>(kind, a, st);
+    case 5: return adj_boundary_d<5>(kind, a, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 template <int D>
 static cudaError_t boundary_d(int kind, bool dev, const BoundaryArgs &a, cudaStream_t st) {
   if (a.nsites <= 0) return cudaSuccess;

@@ -83,6 +83,7 @@ struct BoundaryArgs {
   double ph_c[kMaxModes];  // cos and sin of theta_m - kappa_m . u t_eval
   double ph_s[kMaxModes];
   double omega[kMaxQ];
+  double wratio[kMaxQ];    // omega_k / omega_kbar (adjoint of the half-way scheme)
   double s, oms, R, dt, dx, c;
   double x0[kMaxD];        // coordinate of node 0
   double u[kMaxD];
@@ -137,6 +138,7 @@ struct AdjGradArgs {
 cudaError_t launch_step_fp64(int d, bool adjoint, bool interior, const StepArgs &a, cudaStream_t st);
 cudaError_t launch_step_dev(int d, bool adjoint, bool interior, const StepArgs &a, cudaStream_t st);
 cudaError_t launch_boundary(int d, int kind, bool dev, const BoundaryArgs &a, cudaStream_t st);
+cudaError_t launch_adjoint_boundary(int d, int kind, const BoundaryArgs &a, cudaStream_t st);
 cudaError_t launch_init(int d, bool dev, const InitArgs &a, cudaStream_t st);
 cudaError_t launch_macro_fp64(int d, const StepArgs &a, double *phi_out, cudaStream_t st);
 cudaError_t launch_fd_grad(int d, const Geom &g, double dx, const double *phi, double *grad, cudaStream_t st);

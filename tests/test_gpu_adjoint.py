@@ -129,3 +129,94 @@ def test_autograd_function():
     assert np.max(np.abs(phi0.grad.cpu().numpy() - gphi_o)) < 1e-12 * np.max(np.abs(gphi_o))
     assert np.max(np.abs(R.grad.cpu().numpy() - gR_o)) < 1e-12 * np.max(np.abs(gR_o))
     sim.close()
+
+
+# ------------------------------------------------------------------ Dirichlet boxes (FP64)
+
+def _dirichlet_case(d, bc):
+    n = {2: 8, 3: 6}[d]
+    u = {2: (0.1, -0.2), 3: (0.1, 0.05, -0.15)}[d]
+    wave = (dict(a=[1.0, 0.5], kappa=[(np.pi, np.pi), (2.0, -1.0)], theta=[0.3, 1.1], b=0.2) if d == 2 else
+            dict(a=[0.8], kappa=[(np.pi, 1.0, -2.0)], theta=[0.4], b=-0.1))
+    return n, u, wave
+
+
+def _dirichlet_gpu(d, n, u, tau, bc, wave, phi0, grad, target, T, R=0.7):
+    sim = LBM(d, n, u=u, tau=tau, R=R, bc=bc)
+    sim.init(_t(phi0), _t(grad))
+    sim.set_boundary_wave(wave["a"], wave["kappa"], wave["theta"], wave["b"])
+    sim.step(T)
+    r = sim.macro() - _t(target)
+    loss = 0.5 * float((r * r).sum())
+    sim.adjoint_seed(r.contiguous())
+    sim.adjoint_step(T)
+    gphi, ggrad, _ = sim.adjoint_grads(want_grad=True, want_R=False)
+    sim.close()
+    return loss, gphi.cpu().numpy(), ggrad.cpu().numpy().reshape(-1)
+
+
+@pytest.mark.parametrize("tau", [0.5, 0.8])
+@pytest.mark.parametrize("bc", ["fullway", "halfway"])
+@pytest.mark.parametrize("d", [2, 3])
+def test_fp64_dirichlet_adjoint_matches_the_oracle(d, bc, tau):
+    n, u, wave = _dirichlet_case(d, bc)
+    rng = np.random.default_rng(80 + d)
+    S = n ** d
+    phi0, grad, target = rng.normal(size=S), rng.normal(size=(d, S)), rng.normal(size=S)
+    T = 9
+    m = O.Model(d, n, 0.0, 1.0, u, tau=tau, R=0.7, bc=bc)
+    w = m.wave(**wave)
+    loss_o, gphi_o, _, ggrad_o = m.gradient(phi0, None, target, T, order=3, grad=grad, wave=w)
+    loss_g, gphi_g, ggrad_g = _dirichlet_gpu(d, n, u, tau, bc, wave, phi0, grad, target, T)
+    assert abs(loss_g - loss_o) < 1e-12 * loss_o
+    assert np.max(np.abs(gphi_g - gphi_o)) < 1e-12 * np.max(np.abs(gphi_o))
+    assert np.max(np.abs(ggrad_g - ggrad_o.ravel())) < 1e-12 * np.max(np.abs(ggrad_o))
+
+
+@pytest.mark.parametrize("bc", ["fullway", "halfway"])
+def test_fp64_dirichlet_gradient_central_differences(bc):
+    """The loss is quadratic in (phi0, grad phi0): central differences of the library's own forward
+    runs equal the adjoint gradient up to rounding (16x16 box, 40 steps, 8 random directions)."""
+    d, n, T = 2, 16, 40
+    u = (0.1, -0.2) if bc == "fullway" else (0.01, 0.02)
+    wave = dict(a=[1.0, 0.5], kappa=[(np.pi, np.pi), (2.0, -1.0)], theta=[0.3, 1.1], b=0.2)
+    rng = np.random.default_rng(90)
+    S = n * n
+    phi0, grad, target = rng.normal(size=S), rng.normal(size=(d, S)), rng.normal(size=S)
+    _, gphi, ggrad = _dirichlet_gpu(d, n, u, 0.5, bc, wave, phi0, grad, target, T)
+
+    def loss(p, g):
+        sim = LBM(d, n, u=u, R=0.7, bc=bc)
+        sim.init(_t(p), _t(g))
+        sim.set_boundary_wave(wave["a"], wave["kappa"], wave["theta"], wave["b"])
+        sim.step(T)
+        r = sim.macro().cpu().numpy() - target
+        sim.close()
+        return 0.5 * float(r @ r)
+
+    for trial in range(8):
+        vp, vg = rng.normal(size=S), rng.normal(size=(d, S))
+        h = 1e-3
+        fd = (loss(phi0 + h * vp, grad + h * vg) - loss(phi0 - h * vp, grad - h * vg)) / (2 * h)
+        an = gphi @ vp + float(ggrad @ vg.ravel())
+        assert abs(fd - an) < 1e-6 * max(1.0, abs(an)), (fd, an)
+
+
+def test_dirichlet_adjoint_error_paths():
+    from paper_2410_13165_gb300 import LHEError
+
+    n, u, wave = _dirichlet_case(2, "fullway")
+    dev = LBM(2, n, u=u, bc="fullway", precision="fp32dev")
+    dev.init(_t(np.zeros(n * n)), _t(np.zeros((2, n * n))))
+    with pytest.raises(LHEError) as ei:
+        dev.adjoint_seed(_t(np.ones(n * n)))
+    assert ei.value.status == _abi.ERR_STATE
+    dev.close()
+    sim = LBM(2, n, u=u, bc="fullway")
+    sim.init(_t(np.zeros(n * n)), _t(np.zeros((2, n * n))))
+    sim.adjoint_seed(_t(np.ones(n * n)))
+    sim.adjoint_step(2)
+    with pytest.raises(LHEError) as ei:
+        sim.adjoint_grads(want_R=True)
+    assert ei.value.status == _abi.ERR_ARG
+    sim.close()

@@ -572,6 +572,81 @@ def run_order_law(args):
     return 0
 
 
+def run_examples(args):
+    """Example 2 (tanh bubble, periodic, 2D on [-1, 1]^2 and 3D on [-1/2, 1/2]^3) and Example 3's
+    periodic 4D box: the total kinetic entropy sum_x sum_k f_k^2 / (2 omega_k) over time (conserved
+    when every omega_k > 0, not for u = 0.4 (1, 1, 1, 1) in 4D), and the RMSE convergence rates at
+    T = 1 for the first- and third-order initialisations (Tables 2 and 3 report ~2 and ~4)."""
+    import torch
+
+    from paper_2410_13165_gb300 import LBM, build
+    from paper_2410_13165_gb300 import workloads as W
+
+    build.build()
+
+    def t_(a):
+        return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64).ravel()).cuda()
+
+    def bubble(d, N, u, K, T, every=None, unstable=False):
+        lo, hi = (d - 4) / 2.0, (4 - d) / 2.0
+        dx = (hi - lo) / N
+        X = W.node_coords(d, N, lo, dx)
+        v, g = W.tanh_bubble(X, 0.0, u, lo, hi)
+        sim = LBM(d, N, lo, hi, u=u, init_order=K, allow_unstable=unstable)
+        sim.init(t_(v), t_(g))
+        steps = int(round(T / sim.dt))
+        series = []
+        if every:
+            for n in range(0, steps + 1, every):
+                if n:
+                    sim.step(every)
+                series.append([n * sim.dt, sim.diagnostics()["entropy"]])
+        else:
+            sim.step(steps)
+        ex, _ = W.tanh_bubble(X, steps * sim.dt, u, lo, hi)
+        err = float(np.sqrt(np.mean((sim.macro().cpu().numpy() - ex) ** 2)))
+        sim.close()
+        return err, series
+
+    out = {"metric": "kinetic entropy over time and RMSE rates, Examples 2 and 3", "unit": "rate"}
+    ent = {}
+    for d, N, us in ((2, 200, [(0.1, 0.2), (0.45, 0.45)]), (3, 100, [(0.1, 0.1, 0.1), (0.05, 0.1, 0.08)])):
+        for u in us:
+            _, ser = bubble(d, N, u, 3, 1.0, every=max(1, N // 10))
+            e0 = ser[0][1]
+            ent["D%d_u%s" % (d, ",".join("%g" % x for x in u))] = {
+                "t": [x[0] for x in ser], "entropy_rel_change": [x[1] / e0 - 1.0 for x in ser]}
+    # Example 3, periodic 4D: sin(pi sum_i (x_i - u_i t)) on [-1, 1]^4, 24^4 nodes
+    for uu in (0.05, 0.1, 0.2, 0.4):
+        N, u = 24, (uu,) * 4
+        X = W.node_coords(4, N, -1.0, 2.0 / N)
+        v, g = W.wave_solution(X, 0.0, u, 0.0, a=[1.0], kappa=[(np.pi,) * 4], theta=[0.0])
+        sim = LBM(4, N, -1.0, 1.0, u=u, allow_unstable=True)
+        sim.init(t_(v), t_(g))
+        ser = []
+        for n in range(0, 5 * N + 1, N // 2):
+            if n:
+                sim.step(N // 2)
+            e = sim.diagnostics()["entropy"]
+            ser.append([n * sim.dt, e if np.isfinite(e) else None])
+        ent["D4_u%g" % uu] = {"t": [x[0] for x in ser],
+                              "entropy_rel_change": [None if x[1] is None else x[1] / ser[0][1] - 1.0 for x in ser],
+                              "min_omega": min(sim.omega)}
+        sim.close()
+    out["entropy"] = ent
+    rates = {}
+    for d, Ns, u in ((2, (200, 400, 800, 1600), (0.1, 0.2)), (2, (200, 400, 800, 1600), (0.45, 0.45)),
+                     (3, (150, 180, 210, 240, 270, 300), (0.1, 0.1, 0.1))):
+        for K in (1, 3):
+            errs = [bubble(d, N, u, K, 1.0)[0] for N in Ns]
+            rates["D%d_u%s_K%d" % (d, ",".join("%g" % x for x in u), K)] = {
+                "N": list(Ns), "rmse": errs,
+                "rates": [float(np.log(a / b) / np.log(n2 / n1)) for a, b, n1, n2 in zip(errs, errs[1:], Ns, Ns[1:])]}
+    out["rates"] = rates
+    print(json.dumps(out))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -587,12 +662,13 @@ def main():
     ap.add_argument("--error-steps", type=int, default=2000)
     ap.add_argument("--workload", default="d3q19_256",
                     choices=["d3q19_256", "d4q33_dirichlet", "d5q51_fp32dev", "adjoint", "convergence",
-                             "order_law"])
+                             "order_law", "examples"])
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
     others = {"d4q33_dirichlet": run_d4q33_dirichlet, "d5q51_fp32dev": run_d5q51_fp32dev,
-              "adjoint": run_adjoint_ratio, "convergence": run_convergence, "order_law": run_order_law}
+              "adjoint": run_adjoint_ratio, "convergence": run_convergence, "order_law": run_order_law,
+              "examples": run_examples}
     if args.workload in others:
         if args.steps == 400:
             args.steps = 50

@@ -121,3 +121,22 @@ def wave_solution(X: np.ndarray, t: float, u, R: float, a, kappa, theta, b: floa
         val = val + am * np.sin(arg)
         grad = grad + am * km[:, None] * np.cos(arg)[None, :]
     return val, grad
+
+
+def tanh_bubble(X: np.ndarray, t: float, u, lo, hi):
+    """Example 2's field phi = 1/2 - 1/2 tanh((r0 - |x - u t|) / (2 W)) on the periodic box [lo, hi]^d,
+    r0 = 1/(5(d-1)), W = (5-d)/75, with the distance taken to the nearest periodic image of the
+    moving centre; returns the value and its gradient at the (d, S) coordinates X."""
+    d = X.shape[0]
+    L = np.asarray(hi, dtype=np.float64) - np.asarray(lo, dtype=np.float64)
+    L = np.broadcast_to(L, (d,))
+    r0, W = 1.0 / (5.0 * (d - 1)), (5.0 - d) / 75.0
+    Y = X - np.asarray(u, dtype=np.float64)[:, None] * t
+    Y = Y - L[:, None] * np.round(Y / L[:, None])
+    r = np.sqrt(np.sum(Y * Y, axis=0))
+    z = (r0 - r) / (2.0 * W)
+    val = 0.5 - 0.5 * np.tanh(z)
+    dval_dr = 0.25 / W / np.cosh(z) ** 2
+    with np.errstate(invalid="ignore", divide="ignore"):
+        grad = np.where(r > 0, dval_dr * Y / np.where(r > 0, r, 1.0), 0.0)
+    return val, grad

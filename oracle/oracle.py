@@ -323,3 +323,35 @@ def rmse(phi, phi_exact) -> float:
     """Eq. (rmse): root-mean-square error over all lattice points."""
     d = np.asarray(phi) - np.asarray(phi_exact)
     return float(np.sqrt(np.mean(d * d)))
+
+
+# ---------------------------------------------------------------------- stability maps (Sec. 4)
+
+def amplification_matrix(d: int, sigma, xi, s: float = 2.0, g: float = 0.5) -> np.ndarray:
+    """Eq. (G) in moment space: G(xi) = M T(xi) M^{-1} ((1 - s) I + s eps e_1^T), T = diag(exp(-i c_k . xi))
+    (the i of the Fourier variable restored), eps the EDF moment vector with the m4 rule."""
+    sigma = np.asarray(sigma, dtype=np.float64)
+    M = moment_matrix(d)
+    e = velocities(d)
+    ep = eps(d, sigma, m4_rule(d, sigma, g)) if d > 1 else eps(d, sigma, 0.0)
+    Q = M.shape[0]
+    T = np.diag(np.exp(-1j * (e @ np.asarray(xi, dtype=np.float64))))
+    E1 = np.zeros(Q)
+    E1[0] = 1.0
+    C = (1.0 - s) * np.eye(Q) + s * np.outer(ep, E1)
+    return M @ T @ np.linalg.solve(M, C)
+
+
+def stability_map(d: int, sigmas, nxi: int, tau: float = 0.5, g: float = 0.5):
+    """For each velocity sigma (rows of sigmas): min_k omega_k (Prop. 1: the microscopic entropy
+    conditions are omega_k > 0) and the largest spectral radius of G(xi) over the grid
+    xi_i = -pi + 2 pi j / nxi, j = 0..nxi-1 (von Neumann L2 stability, Sec. 4.2)."""
+    sigmas = np.atleast_2d(np.asarray(sigmas, dtype=np.float64))
+    grid = -np.pi + 2.0 * np.pi * np.arange(nxi) / nxi
+    xis = np.stack(np.meshgrid(*([grid] * d), indexing="ij"), axis=-1).reshape(-1, d)
+    omin, rho = np.empty(len(sigmas)), np.empty(len(sigmas))
+    for p, sig in enumerate(sigmas):
+        m4 = m4_rule(d, sig, g) if d > 1 else 0.0
+        omin[p] = np.min(weights_closed(d, sig, m4))
+        rho[p] = max(np.max(np.abs(np.linalg.eigvals(amplification_matrix(d, sig, xi, 1.0 / tau, g)))) for xi in xis)
+    return rho, omin

@@ -229,3 +229,37 @@ def test_halfway_diverges_where_fullway_converges():
     for e in (full, half_slow, full_fast):
         assert all(a / b > 12.0 for a, b in zip(e, e[1:])), e
     assert half[0] < half[1] < half[2] and half[2] > 1.0, half
+
+
+# ----------------------------------------------------------------- stability maps (Sec. 4)
+
+def test_stability_map_remark4_region_2d():
+    """Remark 4: in 1D and 2D the scheme is microscopic entropy-stable for |sigma_i| < 1/2; there the
+    amplification matrices of Eq. (G) have spectral radius 1 (s = 2 is non-dissipative)."""
+    g = np.array([-0.45, -0.3, -0.1, 0.0, 0.2, 0.35, 0.49])
+    S = np.array([(a, b) for a in g for b in g])
+    rho, omin = O.stability_map(2, S, 12)
+    assert np.all(omin > 0.0)
+    assert np.all(np.abs(rho - 1.0) < 1e-12)
+    rho1, omin1 = O.stability_map(1, [(0.3,), (-0.49,), (0.6,), (-0.9,)], 16)
+    assert np.all(omin1[:2] > 0) and np.all(omin1[2:] < 0)
+    assert np.all(np.abs(rho1[:2] - 1.0) < 1e-12) and np.all(rho1[2:] > 1.05)
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_entropy_region_equals_l2_region(d):
+    """The paper's numerical finding (Sec. 4.2): the region where every omega_k > 0 is the region of
+    von Neumann stability. Checked on a coarse grid of velocities away from the region's boundary
+    (where min omega_k = 0 and the spectral radius is 1 up to rounding)."""
+    if d == 2:
+        g = np.round(np.arange(-0.9, 0.91, 0.15), 10)
+        S = np.array([(a, b) for a in g for b in g])
+        nxi = 12
+    else:
+        g = np.round(np.arange(-0.6, 0.61, 0.3), 10)
+        S = np.array([(a, b, c) for a in g for b in g for c in (0.0, 0.3)])
+        nxi = 6
+    rho, omin = O.stability_map(d, S, nxi)
+    away = np.abs(omin) > 1e-12
+    assert np.count_nonzero(away & (omin < 0)) > 5 and np.count_nonzero(away & (omin > 0)) > 5
+    assert np.all((omin[away] > 0) == (rho[away] <= 1.0 + 1e-9))

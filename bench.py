@@ -647,6 +647,39 @@ def run_examples(args):
     return 0
 
 
+def run_stability_map(args):
+    """Stability maps (Sec. 4) on the GPU: per velocity the smallest EDF weight (entropy conditions,
+    Prop. 1) and the largest spectral radius of Eq. (G) over a xi grid (L2 conditions); the two
+    regions are compared away from the boundary min omega = 0, as the paper states they coincide."""
+    from paper_2410_13165_gb300 import build, stability_map
+
+    build.build()
+    out = {"metric": "stability maps: agreement of the entropy and L2 regions; matrices per second", "unit": "count"}
+    cases = [("D2Q9", 2, np.round(np.linspace(-0.8, 0.8, 161), 12), [None], 32),
+             ("D3Q19", 3, np.round(np.linspace(-0.6, 0.6, 81), 12), [0.0, 0.2, 0.4], 12),
+             ("D4Q33", 4, np.round(np.linspace(-0.4, 0.4, 41), 12), [(0.0, 0.0), (0.1, 0.2)], 6)]
+    for name, d, g, extra, nxi in cases:
+        for x in extra:
+            pts = []
+            for a in g:
+                for b in g:
+                    pts.append((a, b) if d == 2 else ((a, b, x) if d == 3 else (a, b) + tuple(x)))
+            S = np.array(pts)
+            t0 = time.perf_counter()
+            rho, omin = stability_map(d, S, nxi)
+            dt = time.perf_counter() - t0
+            away = np.abs(omin) > 1e-12
+            agree = (omin[away] > 0) == (rho[away] <= 1.0 + 1e-9)
+            key = name if x is None else "%s_slice%s" % (name, x)
+            out[key] = {"points": len(S), "xi_per_point": nxi ** d, "entropy_stable": int(np.sum(omin > 0)),
+                        "l2_stable": int(np.sum(rho <= 1.0 + 1e-9)), "on_boundary": int(np.sum(~away)),
+                        "agree_away_from_boundary": int(agree.sum()), "disagree": int((~agree).sum()),
+                        "max_rho": float(np.max(rho)), "seconds": dt,
+                        "matrices_per_second": len(S) * nxi ** d / dt}
+    print(json.dumps(out))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -662,13 +695,13 @@ def main():
     ap.add_argument("--error-steps", type=int, default=2000)
     ap.add_argument("--workload", default="d3q19_256",
                     choices=["d3q19_256", "d4q33_dirichlet", "d5q51_fp32dev", "adjoint", "convergence",
-                             "order_law", "examples"])
+                             "order_law", "examples", "stability_map"])
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
     others = {"d4q33_dirichlet": run_d4q33_dirichlet, "d5q51_fp32dev": run_d5q51_fp32dev,
               "adjoint": run_adjoint_ratio, "convergence": run_convergence, "order_law": run_order_law,
-              "examples": run_examples}
+              "examples": run_examples, "stability_map": run_stability_map}
     if args.workload in others:
         if args.steps == 400:
             args.steps = 50

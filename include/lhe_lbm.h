@@ -230,6 +230,21 @@ LHE_API lhe_status lhe_lbm_adjoint_step(lhe_lbm *lbm, int64_t n);
  * into dL/dphi0. */
 LHE_API lhe_status lhe_lbm_adjoint_grads(lhe_lbm *lbm, double *dL_dphi0_dev, double *dL_dgrad_dev, double *dL_dR_dev);
 
+/* ---------------- stability maps (Sec. 4) ----------------
+ * For npoints velocities sigma = u/c (sigma_host: npoints*d doubles, point-major, host memory):
+ *   omega_min_host[p] = min_k omega_k(sigma_p), the EDF weights of Eq. (omega_k-2) with the handle-
+ *                       less model given by params (d, tau, m4_mode/g/m4); Prop. 1's microscopic
+ *                       entropy conditions are omega_min > 0;
+ *   rho_max_host[p]   = max over xi in the grid xi_i = -pi + 2 pi j/nxi (j = 0..nxi-1, i = 1..d) of the
+ *                       spectral radius of the amplification matrix G(xi) of Eq. (G) (one step on a
+ *                       Fourier mode; von Neumann L2 stability: rho <= 1). +inf where the eigenvalue
+ *                       iteration did not converge.
+ * Only params->d (1..4), tau, m4_mode, g, m4 and stream are read. Synchronous; allocates and frees
+ * its device scratch. Errors: LHE_ERR_ARG (NULL outputs, d outside 1..4, nxi outside 1..4096,
+ * npoints * nxi^d above 2^40, non-finite sigma), LHE_ERR_CUDA. */
+LHE_API lhe_status lhe_lbm_stability_map(const lhe_lbm_params *p, const double *sigma_host, int64_t npoints,
+                                         int32_t nxi, double *rho_max_host, double *omega_min_host);
+
 #ifdef __cplusplus
 }
 #endif

@@ -54,6 +54,21 @@ def model(d, u, c=1.0, g=0.5, m4=None, allow_unstable=False):
     return _abi.lhe_lbm_model(p, allow_unstable=allow_unstable)
 
 
+def stability_map(d, sigmas, nxi, tau=0.5, g=0.5, m4=None):
+    """Per velocity sigma (rows of sigmas): (rho_max, omega_min) -- the largest spectral radius of the
+    amplification matrix over the xi grid and the smallest EDF weight (lhe_lbm_stability_map)."""
+    import numpy as np
+
+    sig = np.ascontiguousarray(np.atleast_2d(np.asarray(sigmas, dtype=np.float64)))
+    if sig.shape[1] != d:
+        raise ValueError("sigmas must have d columns")
+    p = _params(d, 4, tau=tau, g=g, m4=m4)
+    rho = np.empty(sig.shape[0])
+    omin = np.empty(sig.shape[0])
+    _abi.lhe_lbm_stability_map(p, sig.ctypes.data, sig.shape[0], nxi, rho.ctypes.data, omin.ctypes.data)
+    return rho, omin
+
+
 class LBM:
     """One lattice-Boltzmann problem on the current CUDA device (owns its population buffers)."""
 

@@ -29,7 +29,7 @@ EXPORTS = [
     "lhe_lbm_destroy", "lhe_lbm_last_error", "lhe_lbm_info", "lhe_lbm_set_stream", "lhe_lbm_init",
     "lhe_lbm_set_boundary_wave", "lhe_lbm_step", "lhe_lbm_macro", "lhe_lbm_diagnostics", "lhe_lbm_get_state",
     "lhe_lbm_set_state", "lhe_lbm_adjoint_seed", "lhe_lbm_adjoint_step", "lhe_lbm_adjoint_grads",
-    "lhe_lbm_diagnostics_noalloc",
+    "lhe_lbm_diagnostics_noalloc", "lhe_lbm_stability_map",
 ]
 
 
@@ -106,6 +106,7 @@ def load(path: str | None = None):
         "lhe_lbm_adjoint_step": (st, [_H, ctypes.c_int64]),
         "lhe_lbm_adjoint_grads": (st, [_H, _D, _D, _D]),
         "lhe_lbm_diagnostics_noalloc": (st, [ctypes.POINTER(lhe_lbm_params), _D, _D, _D]),
+        "lhe_lbm_stability_map": (st, [ctypes.POINTER(lhe_lbm_params), _D, ctypes.c_int64, ctypes.c_int32, _D, _D]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -215,3 +216,8 @@ def lhe_lbm_adjoint_grads(h, gphi0_ptr: int, ggrad_ptr: int | None, gR_ptr: int 
 def lhe_lbm_diagnostics_noalloc(p: lhe_lbm_params, pop_ptr: int, R_ptr: int | None, out_ptr: int) -> None:
     """Diagnostics of a caller-owned FP64 state into 4 device doubles, with no device allocation."""
     check(load().lhe_lbm_diagnostics_noalloc(ctypes.byref(p), pop_ptr, R_ptr, out_ptr))
+
+
+def lhe_lbm_stability_map(p: lhe_lbm_params, sigma_ptr: int, npoints: int, nxi: int, rho_ptr: int, omin_ptr: int) -> None:
+    """Stability map of host arrays (see the header): rho_max and omega_min per velocity."""
+    check(load().lhe_lbm_stability_map(ctypes.byref(p), sigma_ptr, int(npoints), int(nxi), rho_ptr, omin_ptr))

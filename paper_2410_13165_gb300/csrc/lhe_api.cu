@@ -817,6 +817,58 @@ lhe_status lhe_lbm_adjoint_step(lhe_lbm *l, int64_t n) {
   return LHE_OK;
 }
 
+lhe_status lhe_lbm_stability_map(const lhe_lbm_params *p, const double *sigma, int64_t npoints, int32_t nxi,
+                                 double *rho_max, double *omega_min) {
+  if (!p || (npoints > 0 && (!sigma || !rho_max || !omega_min))) return fail(nullptr, LHE_ERR_ARG, "NULL argument");
+  const int d = p->d;
+  if (d < 1 || d > 4) return fail(nullptr, LHE_ERR_ARG, "stability maps take d = 1..4");
+  if (npoints < 0) return fail(nullptr, LHE_ERR_ARG, "npoints must be >= 0");
+  if (nxi < 1 || nxi > 4096) return fail(nullptr, LHE_ERR_ARG, "nxi must be in 1..4096");
+  int64_t nper = 1;
+  for (int i = 0; i < d; ++i) nper *= nxi;
+  if (npoints > 0 && nper > ((int64_t)1 << 40) / npoints) return fail(nullptr, LHE_ERR_ARG, "npoints * nxi^d is too large");
+  if (!(p->tau > 0.0) || !std::isfinite(p->tau)) return fail(nullptr, LHE_ERR_ARG, "tau must be positive");
+  if (p->m4_mode != LHE_M4_RULE && p->m4_mode != LHE_M4_EXPLICIT) return fail(nullptr, LHE_ERR_ARG, "unknown m4_mode");
+  if (p->m4_mode == LHE_M4_RULE && !(p->g >= 0.0 && p->g <= 1.0)) return fail(nullptr, LHE_ERR_ARG, "g must be in [0, 1]");
+  if (npoints == 0) return LHE_OK;
+  int32_t e[kMaxQ * kMaxD];
+  const int Q = lattice_vectors(d, e);
+  const int npairs = d * (d - 1) / 2;
+  std::vector<double> om((size_t)npoints * Q);
+  for (int64_t q = 0; q < npoints; ++q) {
+    double sig[kMaxD], m4[10] = {};
+    for (int i = 0; i < d; ++i) {
+      sig[i] = sigma[q * d + i];
+      if (!std::isfinite(sig[i])) return fail(nullptr, LHE_ERR_ARG, "sigma must be finite");
+    }
+    for (int k = 0; k < npairs; ++k) m4[k] = p->m4_mode == LHE_M4_RULE ? m4_rule(d, sig, p->g) : p->m4[k];
+    weights(d, e, Q, sig, m4, &om[(size_t)q * Q]);
+    double mn = om[(size_t)q * Q];
+    for (int k = 1; k < Q; ++k) mn = std::fmin(mn, om[(size_t)q * Q + k]);
+    omega_min[q] = mn;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(p->stream);
+  double *dom = nullptr;
+  unsigned long long *drho = nullptr;
+  auto release = [&]() {
+    cudaFree(dom);
+    cudaFree(drho);
+  };
+  cudaError_t e1 = cudaMalloc(&dom, sizeof(double) * om.size());
+  if (e1 == cudaSuccess) e1 = cudaMalloc(&drho, sizeof(unsigned long long) * (size_t)npoints);
+  if (e1 == cudaSuccess) e1 = cudaMemcpyAsync(dom, om.data(), sizeof(double) * om.size(), cudaMemcpyHostToDevice, st);
+  if (e1 == cudaSuccess) e1 = cudaMemsetAsync(drho, 0, sizeof(unsigned long long) * (size_t)npoints, st);
+  if (e1 == cudaSuccess) e1 = launch_stability(d, dom, npoints, nxi, 1.0 / p->tau, drho, st);
+  std::vector<unsigned long long> bits((size_t)npoints);
+  if (e1 == cudaSuccess)
+    e1 = cudaMemcpyAsync(bits.data(), drho, sizeof(unsigned long long) * bits.size(), cudaMemcpyDeviceToHost, st);
+  if (e1 == cudaSuccess) e1 = cudaStreamSynchronize(st);
+  release();
+  if (e1 != cudaSuccess) return cuda_fail(nullptr, e1, "stability map");
+  for (int64_t q = 0; q < npoints; ++q) std::memcpy(&rho_max[q], &bits[(size_t)q], sizeof(double));
+  return LHE_OK;
+}
+
 lhe_status lhe_lbm_adjoint_grads(lhe_lbm *l, double *gphi0, double *ggrad, double *gR) {
   if (lhe_status s = check_handle(l)) return s;
   if (!l->adj_ready) return fail(l, LHE_ERR_STATE, "lhe_lbm_adjoint_grads before lhe_lbm_adjoint_seed");

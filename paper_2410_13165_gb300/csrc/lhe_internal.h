@@ -139,6 +139,8 @@ cudaError_t launch_step_fp64(int d, bool adjoint, bool interior, const StepArgs 
 cudaError_t launch_step_dev(int d, bool adjoint, bool interior, const StepArgs &a, cudaStream_t st);
 cudaError_t launch_boundary(int d, int kind, bool dev, const BoundaryArgs &a, cudaStream_t st);
 cudaError_t launch_adjoint_boundary(int d, int kind, const BoundaryArgs &a, cudaStream_t st);
+cudaError_t launch_stability(int d, const double *omega_dev, int64_t npoints, int32_t nxi, double s,
+                             unsigned long long *rho_bits_dev, cudaStream_t st);
 cudaError_t launch_init(int d, bool dev, const InitArgs &a, cudaStream_t st);
 cudaError_t launch_macro_fp64(int d, const StepArgs &a, double *phi_out, cudaStream_t st);
 cudaError_t launch_fd_grad(int d, const Geom &g, double dx, const double *phi, double *grad, cudaStream_t st);

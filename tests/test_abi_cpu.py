@@ -97,3 +97,39 @@ def test_binding_refuses_a_missing_library(tmp_path):
         _abi._lib = None
         _abi.load(str(tmp_path / "nope.so"))
     _abi._lib = None
+
+
+def test_create_rejects_oversized_and_unknown_flag_arguments_before_touching_the_device(lib):
+    """Size and argument checks of lhe_lbm_create run before any CUDA call, so they hold on a machine
+    without a GPU: a lattice above 2^31 - 1 nodes (32-bit node indices), unknown flag bits."""
+    p = _abi.lhe_lbm_default_params()
+    p.d = 3
+    for i, n in enumerate((2048, 2048, 1024)):   # 2^32 nodes on a square lattice
+        p.n[i], p.lo[i], p.hi[i] = n, 0.0, float(n)
+    with pytest.raises(_abi.LHEError) as ei:
+        _abi.lhe_lbm_create(p)
+    assert ei.value.status == _abi.ERR_ARG
+    assert b"2^31" in lib.lhe_lbm_last_error(None)
+    q = _abi.lhe_lbm_default_params()
+    q.flags = 0x4
+    with pytest.raises(_abi.LHEError) as ei:
+        _abi.lhe_lbm_create(q)
+    assert ei.value.status == _abi.ERR_ARG
+
+
+def test_stability_map_argument_checks_without_a_device(lib):
+    """lhe_lbm_stability_map validates its arguments on the host (no device work for bad input or
+    an empty batch)."""
+    import ctypes
+
+    p = _abi.lhe_lbm_default_params()
+    p.d = 5
+    sig = (ctypes.c_double * 5)()
+    out = (ctypes.c_double * 1)()
+    st = lib.lhe_lbm_stability_map(ctypes.byref(p), ctypes.addressof(sig), 1, 4, ctypes.addressof(out),
+                                   ctypes.addressof(out))
+    assert st == _abi.ERR_ARG
+    p.d = 2
+    assert lib.lhe_lbm_stability_map(ctypes.byref(p), ctypes.addressof(sig), 1, 0, ctypes.addressof(out),
+                                     ctypes.addressof(out)) == _abi.ERR_ARG
+    assert lib.lhe_lbm_stability_map(ctypes.byref(p), None, 0, 8, None, None) == _abi.OK

@@ -125,7 +125,7 @@ def test_autograd_function():
     m = O.Model(d, n, 0.0, 1.0, (0.1, 0.2))
     lo, gphi_o, gR_o, _ = m.gradient(phi0.detach().cpu().numpy(), R.detach().cpu().numpy(),
                                      target.cpu().numpy(), T)
-    assert abs(float(loss) - lo) < 1e-12 * lo
+    assert abs(float(loss.detach()) - lo) < 1e-12 * lo
     assert np.max(np.abs(phi0.grad.cpu().numpy() - gphi_o)) < 1e-12 * np.max(np.abs(gphi_o))
     assert np.max(np.abs(R.grad.cpu().numpy() - gR_o)) < 1e-12 * np.max(np.abs(gR_o))
     sim.close()

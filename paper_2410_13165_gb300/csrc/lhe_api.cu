@@ -501,7 +501,11 @@ lhe_status lhe_lbm_init(lhe_lbm *l, const double *phi0, const double *grad, cons
   a.Rfield = l->Rfield;
   a.dst = l->pop[0];
   a.phi_dst = l->phi[0];
-  for (int k = 0; k < l->Q; ++k) a.omega[k] = l->omega[k];
+  for (int k = 0; k < l->Q; ++k) {
+    a.omega[k] = l->omega[k];
+    a.c1[k] = (1.0 - l->s) * 0.5 * l->dt * l->omega[k];
+    a.c2[k] = l->p.c * a.c1[k];
+  }
   a.s = l->s;
   a.oms = 1.0 - l->s;
   a.dt = l->dt;

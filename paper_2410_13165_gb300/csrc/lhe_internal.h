@@ -106,6 +106,8 @@ struct InitArgs {
   void *dst;
   float2 *phi_dst;
   double omega[kMaxQ];
+  double c1[kMaxQ];        // (1 - s)(dt/2) omega_k
+  double c2[kMaxQ];        // c (1 - s)(dt/2) omega_k
   double s, oms, dt, dtR, c;
   double u[kMaxD];
   int32_t order;

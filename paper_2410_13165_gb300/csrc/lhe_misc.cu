@@ -7,9 +7,12 @@ namespace lhe {
 
 // ------------------------------------------------------------------------------ initialisation
 // Eq. (ini-simp): f_k(x,0) = omega_k [phi0 + (dt/2)(u - c e_k) . grad phi0] (order 3) or
-// omega_k phi0 (order 1); the stored state is post-collision:
-//   f*_k = (1 - s) f_k + omega_k (s phi0 + dt R(x))            (FP64)
-//   g*_k = f*_k - omega_k phi0 = (1 - s)(f_k - omega_k phi0) + dt omega_k R(x),  phi = phi0   (FP32_DEV)
+// omega_k phi0 (order 1); the stored state is post-collision. With A = phi0 + dt R(x) and the first
+// moment of the correction vanishing (sum_k omega_k (u - c e_k) = 0), the collision
+// f*_k = (1 - s) f_k + omega_k (s phi0 + dt R) is
+//   f*_k = omega_k A + (1 - s)(dt/2) omega_k [u . grad phi0 - c e_k . grad phi0]     (FP64)
+//   g*_k = f*_k - omega_k phi0 = omega_k dt R + (same correction),  phi = phi0      (FP32_DEV)
+// three FP64 operations per population (c1_k = (1 - s)(dt/2) omega_k, c2_k = c c1_k on the host).
 template <int D, bool DEV>
 __global__ void __launch_bounds__(256) k_init(const InitArgs a) {
   constexpr Lattice<D> L{};
@@ -20,20 +23,24 @@ __global__ void __launch_bounds__(256) k_init(const InitArgs a) {
   const double phi0 = a.phi0[site];
   const double dtR = a.Rfield ? a.dt * a.Rfield[site] : a.dtR;
   double gr[D];
+  double ug = 0.0;
 #pragma unroll
-  for (int i = 0; i < D; ++i) gr[i] = (a.order == 3) ? a.grad[i * S + site] : 0.0;
+  for (int i = 0; i < D; ++i) {
+    gr[i] = (a.order == 3) ? a.grad[i * S + site] : 0.0;
+    ug = fma(a.u[i], gr[i], ug);
+  }
+  const double A = DEV ? dtR : phi0 + dtR;
 #pragma unroll
   for (int k = 0; k < Q; ++k) {
-    double dot = 0.0;
+    double eg = 0.0;  // e_k . grad phi0 (components are 0 or +-1)
 #pragma unroll
-    for (int i = 0; i < D; ++i) dot = fma(a.u[i] - a.c * L.e[k][i], gr[i], dot);
-    const double dev = a.omega[k] * (0.5 * a.dt * dot);  // f_k - omega_k phi0
-    if (DEV) {
-      static_cast<float *>(a.dst)[k * S + site] = (float)fma(a.oms, dev, a.omega[k] * dtR);
-    } else {
-      const double fk = fma(a.omega[k], phi0, dev);
-      static_cast<double *>(a.dst)[k * S + site] = fma(a.omega[k], fma(a.s, phi0, dtR), a.oms * fk);
+    for (int i = 0; i < D; ++i) {
+      if (L.e[k][i] == 1) eg += gr[i];
+      if (L.e[k][i] == -1) eg -= gr[i];
     }
+    const double v = fma(a.omega[k], A, fma(-a.c2[k], eg, a.c1[k] * ug));
+    if (DEV) static_cast<float *>(a.dst)[k * S + site] = (float)v;
+    else static_cast<double *>(a.dst)[k * S + site] = v;
   }
   if (DEV) a.phi_dst[site] = df_split(phi0);
 }

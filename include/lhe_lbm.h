@@ -77,6 +77,12 @@ typedef enum { LHE_M4_RULE = 0, LHE_M4_EXPLICIT = 1 } lhe_m4_mode;
  * by bulk asynchronous copies (both compute the same bits; the staged one is the default where
  * its layout conditions hold: n_1 a multiple of 4 and at most 512). */
 #define LHE_FLAG_NO_STAGING 1
+/* LHE_FLAG_NO_PDL: launch every step kernel with plain stream ordering. By default the second and
+ * later step kernels of one lhe_lbm_step / lhe_lbm_adjoint_step call are launched with programmatic
+ * stream serialization: such a kernel may be scheduled while the step before it finishes, and waits
+ * for that step to complete before it touches global memory (same results, shorter gaps between
+ * consecutive steps). The first kernel of a call is always ordered plainly behind the stream. */
+#define LHE_FLAG_NO_PDL 2
 
 typedef struct {
   int32_t d;              /* spatial dimension, 1..5 */

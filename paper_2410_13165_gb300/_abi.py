@@ -22,6 +22,7 @@ BC_PERIODIC, BC_FULLWAY, BC_HALFWAY = 0, 1, 2
 FP64, FP32_DEV = 0, 1
 M4_RULE, M4_EXPLICIT = 0, 1
 FLAG_NO_STAGING = 1
+FLAG_NO_PDL = 2
 
 # every entry point declared in include/lhe_lbm.h
 EXPORTS = [

@@ -116,7 +116,7 @@ lhe_status build_model(const lhe_lbm_params *p, Model &m, lhe_lbm *err_to) {
     return fail(err_to, LHE_ERR_ARG, "half-way bc_order must be 1..4");
   if (!(p->c > 0.0) || !std::isfinite(p->c)) return fail(err_to, LHE_ERR_ARG, "c must be positive");
   if (!(p->tau > 0.0) || !std::isfinite(p->tau)) return fail(err_to, LHE_ERR_ARG, "tau must be positive");
-  if (p->flags & ~LHE_FLAG_NO_STAGING) return fail(err_to, LHE_ERR_ARG, "unknown bits in flags");
+  if (p->flags & ~(LHE_FLAG_NO_STAGING | LHE_FLAG_NO_PDL)) return fail(err_to, LHE_ERR_ARG, "unknown bits in flags");
   if (p->m4_mode != LHE_M4_RULE && p->m4_mode != LHE_M4_EXPLICIT) return fail(err_to, LHE_ERR_ARG, "unknown m4_mode");
   if (p->m4_mode == LHE_M4_RULE && !(p->g >= 0.0 && p->g <= 1.0)) return fail(err_to, LHE_ERR_ARG, "g must be in [0, 1]");
   double dxs[kMaxD];
@@ -195,6 +195,7 @@ StepArgs step_args(const lhe_lbm *l) {
   a.rho_dtR = a.dtR;
   a.gsc = a.dt;
   a.pscale = 1.0;
+  a.pdl = 0;
   return a;
 }
 
@@ -279,6 +280,10 @@ lhe_status check_pipeline(lhe_lbm *l) {
     return fail(l, LHE_ERR_CUDA, "a staged step kernel timed out waiting for its copies; the state is invalid");
   return LHE_OK;
 }
+
+// Programmatic dependent launch between the consecutive step kernels of one step / adjoint_step call
+// (the first launch of a call keeps plain stream ordering behind whatever the caller queued).
+bool pdl_ok(const lhe_lbm *l) { return !(l->p.flags & LHE_FLAG_NO_PDL); }
 
 lhe_status check_handle(lhe_lbm *l) {
   if (!l) return fail(nullptr, LHE_ERR_ARG, "handle is NULL");
@@ -671,6 +676,7 @@ lhe_status lhe_lbm_step(lhe_lbm *l, int64_t n) {
     a.phi_src = l->phi[l->cur];
     a.phi_dst = l->phi[1 - l->cur];
     a.nwork = periodic ? l->g.S : l->g.S_rows;
+    a.pdl = it > 0 && pdl_ok(l);
     cudaError_t e = l->staged ? launch_step_dev3_tma(false, a, l->tma, l->stream)
                     : dev         ? launch_step_dev(d, false, !periodic, a, l->stream)
                                   : launch_step_fp64(d, false, !periodic, a, l->stream);
@@ -806,6 +812,7 @@ lhe_status lhe_lbm_adjoint_step(lhe_lbm *l, int64_t n) {
     a.dst = l->adj[1 - l->acur];
     a.phi_src = l->adjW[l->acur];
     a.phi_dst = l->adjW[1 - l->acur];
+    a.pdl = it > 0 && pdl_ok(l);
     cudaError_t e = l->staged ? launch_step_dev3_tma(true, a, l->tma, l->stream)
                     : dev         ? launch_step_dev(l->p.d, true, !periodic, a, l->stream)
                                   : launch_step_fp64(l->p.d, true, !periodic, a, l->stream);

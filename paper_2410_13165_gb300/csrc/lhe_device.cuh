@@ -179,4 +179,11 @@ __device__ __forceinline__ float2 df_add(float h, float t) {
 __device__ __forceinline__ void st_stream(double *p, double v) { __stcs(p, v); }
 __device__ __forceinline__ void st_stream(float *p, float v) { __stcs(p, v); }
 
+// Programmatic dependent launch. A step kernel lets the next kernel of its stream be scheduled as
+// soon as every CTA of this one is running (pdl_trigger), and waits for the kernel before it to
+// complete, with its memory visible, before it touches global memory (pdl_wait). When the kernel was
+// launched without the programmatic-serialization attribute both are no-ops.
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 }  // namespace lhe

@@ -5,6 +5,7 @@
 
 #include <cstdint>
 #include <string>
+#include <utility>
 
 #include "lhe_device.cuh"
 #include "lhe_lbm.h"
@@ -43,8 +44,28 @@ struct StepArgs {
   double mu, sig, rho_dt, rho_dtR, gsc;
   double pscale;           // macro: factor from the stored populations to f* (1 unless scaled)
   int32_t collide;         // kCollideGeneral / kCollideScaled (s != 2 only)
+  int32_t pdl;             // launch with programmatic stream serialization (the kernel calls pdl_wait)
   int64_t nwork;           // number of sites processed (S, or the interior count)
 };
+
+// Launch `kernel` on `st`; with pdl set, with the programmatic-stream-serialization attribute, so
+// that it may be scheduled while the previous kernel of the stream finishes (the kernel must call
+// pdl_wait before it touches global memory).
+template <typename... KArgs, typename... Args>
+cudaError_t launch_kernel(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, bool pdl,
+                          Args &&...args) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl ? 1u : 0u;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 
 // Plan of the staged FP32-deviation step on periodic D3Q19 boxes (lhe_step_dev_tma.cu).
 constexpr int kTmaMaxStages = 4;

@@ -25,6 +25,8 @@ template <int D, bool ADJ, bool INTERIOR, bool S2>
 __global__ void __launch_bounds__(LHE_STEP_THREADS) k_step_dev(const StepArgs a) {
   constexpr Lattice<D> L{};
   constexpr int Q = Lattice<D>::Q;
+  pdl_trigger();
+  pdl_wait();
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= a.nwork) return;
   int x[D];
@@ -75,11 +77,8 @@ static cudaError_t launch_step_dev_t(const StepArgs &a, cudaStream_t st) {
   if (a.nwork <= 0) return cudaSuccess;
   const int threads = LHE_STEP_THREADS;
   const unsigned blocks = (unsigned)((a.nwork + threads - 1) / threads);
-  if (a.s == 2.0)
-    k_step_dev<D, ADJ, INTERIOR, true><<<blocks, threads, 0, st>>>(a);
-  else
-    k_step_dev<D, ADJ, INTERIOR, false><<<blocks, threads, 0, st>>>(a);
-  return cudaGetLastError();
+  if (a.s == 2.0) return launch_kernel(k_step_dev<D, ADJ, INTERIOR, true>, blocks, threads, 0, st, a.pdl != 0, a);
+  return launch_kernel(k_step_dev<D, ADJ, INTERIOR, false>, blocks, threads, 0, st, a.pdl != 0, a);
 }
 
 template <int D>

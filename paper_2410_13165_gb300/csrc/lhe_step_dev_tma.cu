@@ -12,7 +12,9 @@
 // complete on its stage's "full" mbarrier; the consumer warps compute the tile and release the
 // stage on its "empty" mbarrier, after which the producer refills it. NS stages rotate, one
 // persistent CTA per SM walks the tiles blockIdx.x, blockIdx.x + gridDim.x, ... and no block-wide
-// barrier is taken inside the loop.
+// barrier is taken inside the loop. Within one call of several steps, a step's kernel is scheduled
+// while the previous one finishes and sets up its barriers before it waits for it (programmatic
+// dependent launch).
 //
 // Every mbarrier wait is bounded in time; on expiry the kernel stops, records the failure in a
 // host-visible flag, waits (bounded) for its copies in flight and returns.
@@ -94,17 +96,28 @@ __device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier
 
 __device__ __forceinline__ int wrap(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
 
-// Issues the copies of tile number i of this CTA into stage s (warp 0; lane 0 arms the barrier).
-// Lane k < Q copies the R source rows of g*_k, lanes Q..Q+2 the R+2 phi rows of the planes
-// z-1, z, z+1; rows that are consecutive in y are one copy (a run breaks only where y wraps).
+// Tile number T of the launch (T = blockIdx.x + i gridDim.x): block ty of R rows in y of plane z.
+struct TileRef {
+  int ty, z;
+};
+
+__device__ __forceinline__ TileRef tile_ref(const DevTmaPlan &p, int T) {
+  TileRef t;
+  t.z = T / p.tiles_y;
+  t.ty = T - t.z * p.tiles_y;
+  return t;
+}
+
+// Issues the copies of tile t into stage s (the producer warp; lane 0 arms the barrier). Lane k < Q
+// copies the R source rows of g*_k, lanes Q..Q+2 the R+2 phi rows of the planes z-1, z, z+1; rows
+// that are consecutive in y are one copy (a run breaks only where y wraps).
 template <bool ADJ>
 __device__ __forceinline__ void issue_tile(const StepArgs &a, const DevTmaPlan &p, unsigned char *smem, uint32_t bar,
-                                           int i, int s, int lane) {
+                                           TileRef t, int s, int lane) {
   constexpr int Q = Lattice<3>::Q;
   const int sgn = ADJ ? -1 : 1;
-  const int tile = (int)blockIdx.x + i * (int)gridDim.x;
-  const int ty = tile % p.tiles_y, z = tile / p.tiles_y;
-  const int y0 = ty * p.R;
+  const int z = t.z;
+  const int y0 = t.ty * p.R;
   const uint32_t stage = smem_u32(smem) + (uint32_t)s * p.stage_bytes;
   if (lane == 0) mbar_arrive_expect_tx(bar, p.tx_bytes);
   __syncwarp();
@@ -154,6 +167,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_step_dev3_tma(const StepArgs
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
   const int my = p.ntiles > (int)blockIdx.x ? (p.ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+  pdl_trigger();
   if (tid == 0) {
     for (int s = 0; s < p.NS; ++s) {
       mbar_init(smem_u32(&full[s]), 1u);
@@ -163,6 +177,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_step_dev3_tma(const StepArgs
     fence_proxy_async();
     abort_flag = 0;
   }
+  pdl_wait();  // the barriers are set up while the previous step finishes
   __syncthreads();
 
   if (warp == kConsumerWarps) {
@@ -170,6 +185,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_step_dev3_tma(const StepArgs
     int i = 0;
     for (; i < my; ++i) {
       const int s = i % p.NS;
+      const TileRef t = tile_ref(p, (int)blockIdx.x + i * (int)gridDim.x);
       if (i >= p.NS) {
         bool ok = true;
         if (lane == 0) ok = mbar_wait(smem_u32(&empty[s]), (uint32_t)((i / p.NS - 1) & 1));
@@ -179,7 +195,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_step_dev3_tma(const StepArgs
           break;
         }
       }
-      issue_tile<ADJ>(a, p, smem, smem_u32(&full[s]), i, s, lane);
+      issue_tile<ADJ>(a, p, smem, smem_u32(&full[s]), t, s, lane);
     }
     if (lane == 0) {
       if (*(volatile int *)&abort_flag) {
@@ -197,7 +213,6 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_step_dev3_tma(const StepArgs
 
   // consumer warps
   const int sgn = ADJ ? -1 : 1;
-  float *__restrict__ dst = static_cast<float *>(a.dst);
   const int64_t S = a.g.S;
   const float oms = (float)a.oms;
   const bool field = !ADJ && a.Rfield != nullptr;
@@ -208,9 +223,11 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_step_dev3_tma(const StepArgs
       if (tid == 0) *p.err = 1;
       break;
     }
-    const int tile = (int)blockIdx.x + i * (int)gridDim.x;
-    const int ty = tile % p.tiles_y, z = tile / p.tiles_y;
-    const int y0 = ty * p.R;
+    const TileRef t = tile_ref(p, (int)blockIdx.x + i * (int)gridDim.x);
+    float *__restrict__ dst = static_cast<float *>(a.dst);
+    float2 *__restrict__ phi_dst = a.phi_dst;
+    const int z = t.z;
+    const int y0 = t.ty * p.R;
     const float *G = reinterpret_cast<const float *>(smem + (size_t)s * p.stage_bytes);
     const float2 *P = reinterpret_cast<const float2 *>(smem + (size_t)s * p.stage_bytes + p.g_bytes);
     const double *X = reinterpret_cast<const double *>(smem + (size_t)s * p.stage_bytes + p.g_bytes + p.phi_bytes);
@@ -244,7 +261,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_step_dev3_tma(const StepArgs
       }
       const float Delta = accw + accg;
       const float2 pn = df_add(p0.x, p0.y + Delta);
-      a.phi_dst[site] = pn;
+      phi_dst[site] = pn;
       if (ADJ && a.gR) a.gR[site] = fma(a.dt, df_value(pn), X[idx]);
       float dtR = 0.0f;
       if (field) dtR = (float)(a.dt * X[idx]);
@@ -314,14 +331,9 @@ cudaError_t launch_step_dev3_tma(bool adjoint, const StepArgs &a, const DevTmaPl
   p.tx_bytes = p.g_bytes + p.phi_bytes + (with_x ? p.x_bytes : 0u);
   const size_t bytes = (size_t)p.NS * p.stage_bytes;
   const bool s2 = a.s == 2.0;
-  if (adjoint) {
-    if (s2) k_step_dev3_tma<true, true><<<p.grid, kTmaThreads, bytes, st>>>(a, p);
-    else k_step_dev3_tma<true, false><<<p.grid, kTmaThreads, bytes, st>>>(a, p);
-  } else {
-    if (s2) k_step_dev3_tma<false, true><<<p.grid, kTmaThreads, bytes, st>>>(a, p);
-    else k_step_dev3_tma<false, false><<<p.grid, kTmaThreads, bytes, st>>>(a, p);
-  }
-  return cudaGetLastError();
+  auto kernel = adjoint ? (s2 ? k_step_dev3_tma<true, true> : k_step_dev3_tma<true, false>)
+                        : (s2 ? k_step_dev3_tma<false, true> : k_step_dev3_tma<false, false>);
+  return launch_kernel(kernel, p.grid, kTmaThreads, bytes, st, a.pdl != 0, a, p);
 }
 
 }  // namespace lhe

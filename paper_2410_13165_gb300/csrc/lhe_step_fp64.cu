@@ -24,6 +24,8 @@ template <int D, bool ADJ, bool INTERIOR, int MODE>
 __global__ void __launch_bounds__(LHE_STEP_THREADS) k_step_fp64(const StepArgs a) {
   constexpr Lattice<D> L{};
   constexpr int Q = Lattice<D>::Q;
+  pdl_trigger();
+  pdl_wait();
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= a.nwork) return;
   int x[D];
@@ -81,13 +83,11 @@ static cudaError_t launch_step_fp64_t(const StepArgs &a, cudaStream_t st) {
   if (a.nwork <= 0) return cudaSuccess;
   const int threads = LHE_STEP_THREADS;
   const unsigned blocks = (unsigned)((a.nwork + threads - 1) / threads);
-  if (a.s == 2.0)
-    k_step_fp64<D, ADJ, INTERIOR, kModeS2><<<blocks, threads, 0, st>>>(a);
-  else if (a.collide == kCollideScaled)
-    k_step_fp64<D, ADJ, INTERIOR, kModeScaled><<<blocks, threads, 0, st>>>(a);
-  else
-    k_step_fp64<D, ADJ, INTERIOR, kModeGeneral><<<blocks, threads, 0, st>>>(a);
-  return cudaGetLastError();
+  const bool pdl = a.pdl != 0;
+  if (a.s == 2.0) return launch_kernel(k_step_fp64<D, ADJ, INTERIOR, kModeS2>, blocks, threads, 0, st, pdl, a);
+  if (a.collide == kCollideScaled)
+    return launch_kernel(k_step_fp64<D, ADJ, INTERIOR, kModeScaled>, blocks, threads, 0, st, pdl, a);
+  return launch_kernel(k_step_fp64<D, ADJ, INTERIOR, kModeGeneral>, blocks, threads, 0, st, pdl, a);
 }
 
 template <int D>

@@ -121,3 +121,57 @@ def test_staged_step_full_size_256():
         res.append(sim.get_state().clone())
         sim.close()
     assert torch.equal(res[0], res[1])
+
+
+def _seq_states(n, tau, calls, staged, seed=0, adjoint_calls=(), pdl=True):
+    """State and phi after a sequence of step(k) calls (then adjoint_step calls, if any)."""
+    import torch
+
+    phi0, grad = _problem(n, seed)
+    sim = LBM(3, list(n), 0.0, [ni / 32.0 for ni in n], u=(0.1, -0.05, 0.08), tau=tau, precision="fp32dev",
+              staged=staged, pdl=pdl)
+    sim.init(_t(phi0), _t(grad))
+    for k in calls:
+        sim.step(k)
+    out = [sim.get_state().clone(), sim.macro().clone()]
+    if adjoint_calls:
+        sim.adjoint_seed(sim.macro().contiguous())
+        for k in adjoint_calls:
+            sim.adjoint_step(k)
+        gphi, _, gR = sim.adjoint_grads(want_grad=False, want_R=True)
+        out += [gphi.clone(), gR.clone()]
+    sim.close()
+    torch.cuda.synchronize()
+    return out
+
+
+@pytest.mark.parametrize("n,calls", [((16, 12, 8), [5, 1, 2, 7, 1, 3]), ((8, 3, 4), [2, 2, 9]),
+                                     ((32, 6, 5), [1, 1, 6, 11]), ((12, 20, 7), [17])])
+def test_consecutive_launches_in_one_call_are_bitwise_single_calls(n, calls):
+    """Within one step(k) / adjoint_step(k) call the step kernels after the first are launched with
+    programmatic dependent launch; the result must equal k calls of one step, plain stream ordering
+    (LHE_FLAG_NO_PDL) and the register kernel, over call sequences that mix both."""
+    import torch
+
+    ref = _seq_states(n, 0.8, [1] * sum(calls), True, seed=sum(n), adjoint_calls=[1] * 6)
+    run = _seq_states(n, 0.8, calls, True, seed=sum(n), adjoint_calls=[2, 3, 1])
+    plain = _seq_states(n, 0.8, calls, True, seed=sum(n), adjoint_calls=[2, 3, 1], pdl=False)
+    reg = _seq_states(n, 0.8, calls, False, seed=sum(n), adjoint_calls=[6])
+    for a, b, c, d in zip(ref, run, plain, reg):
+        assert torch.equal(a, b) and torch.equal(a, c) and torch.equal(a, d)
+
+
+def test_staged_step_128_matches_register_kernel():
+    """The precision workload's grid (D3Q19 128^3, tau = 0.8), 12 steps in one call."""
+    import torch
+
+    n = 128
+    phi0, grad, _, _ = W.periodic_problem(3, n, 8, 2)
+    res = []
+    for staged in (True, False):
+        sim = LBM(3, n, u=(0.1, 0.1, 0.1), tau=0.8, precision="fp32dev", staged=staged)
+        sim.init(_t(phi0), _t(grad))
+        sim.step(12)
+        res.append((sim.get_state().clone(), sim.macro().clone()))
+        sim.close()
+    assert torch.equal(res[0][0], res[1][0]) and torch.equal(res[0][1], res[1][1])

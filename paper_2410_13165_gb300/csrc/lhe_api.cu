@@ -396,8 +396,17 @@ lhe_status lhe_lbm_create(const lhe_lbm_params *p, lhe_lbm **out) {
     }
     std::sort(keyed.begin(), keyed.end());
     std::vector<int32_t> sites(keyed.size());
-    for (size_t j = 0; j < keyed.size(); ++j) sites[j] = keyed[j].second;
+    l->nb_xface = 0;
+    for (size_t j = 0; j < keyed.size(); ++j) {
+      sites[j] = keyed[j].second;
+      if (keyed[j].first <= 2) ++l->nb_xface;  // signatures 1 and 2 (x_1 face only) sort first
+    }
     l->nb = (int64_t)sites.size();
+    if (p->precision == LHE_FP64) {
+      const int64_t nrows = l->g.S_rows / l->g.n[0];
+      e = cudaMalloc(&l->xface, sizeof(double) * (size_t)(2 * nrows * (2 * p->d - 1)));
+      if (e != cudaSuccess) return bail(cuda_fail(l, e, "cudaMalloc(x-face boundary data)"));
+    }
     e = cudaMalloc(&l->bsites, sizeof(int32_t) * sites.size());
     if (e != cudaSuccess) return bail(cuda_fail(l, e, "cudaMalloc(boundary nodes)"));
     e = cudaMemcpy(l->bsites, sites.data(), sizeof(int32_t) * sites.size(), cudaMemcpyHostToDevice);
@@ -441,6 +450,7 @@ lhe_status lhe_lbm_destroy(lhe_lbm *l) {
   cudaFree(l->Rfield);
   cudaFree(l->fdgrad);
   cudaFree(l->bsites);
+  cudaFree(l->xface);
   cudaFree(l->bc_table);
   cudaFree(l->bc_axis);
   cudaFree(l->red_partials);
@@ -677,10 +687,6 @@ lhe_status lhe_lbm_step(lhe_lbm *l, int64_t n) {
     a.phi_dst = l->phi[1 - l->cur];
     a.nwork = periodic ? l->g.S : l->g.S_rows;
     a.pdl = it > 0 && pdl_ok(l);
-    cudaError_t e = l->staged ? launch_step_dev3_tma(false, a, l->tma, l->stream)
-                    : dev         ? launch_step_dev(d, false, !periodic, a, l->stream)
-                                  : launch_step_fp64(d, false, !periodic, a, l->stream);
-    if (e != cudaSuccess) return cuda_fail(l, e, "step kernel launch");
     if (!periodic) {
       b.src = a.src;
       b.dst = a.dst;
@@ -693,7 +699,21 @@ lhe_status lhe_lbm_step(lhe_lbm *l, int64_t n) {
         b.ph_c[m] = std::cos(ph);
         b.ph_s[m] = std::sin(ph);
       }
-      e = launch_boundary(d, l->p.bc, dev, b, l->stream);
+    }
+    // FP64 Dirichlet boxes: the row kernel also treats the x_1-face nodes of its rows
+    const bool fused = !periodic && !dev && !a.Rfield && l->xface;
+    cudaError_t e = l->staged ? launch_step_dev3_tma(false, a, l->tma, l->stream)
+                    : fused       ? launch_step_box_fp64(d, l->p.bc, a, b, l->xface, l->g.S_rows / l->g.n[0], l->stream)
+                    : dev         ? launch_step_dev(d, false, !periodic, a, l->stream)
+                                  : launch_step_fp64(d, false, !periodic, a, l->stream);
+    if (e != cudaSuccess) return cuda_fail(l, e, "step kernel launch");
+    if (!periodic) {
+      BoundaryArgs rest = b;
+      if (fused) {
+        rest.sites = b.sites + l->nb_xface;
+        rest.nsites = b.nsites - l->nb_xface;
+      }
+      e = launch_boundary(d, l->p.bc, dev, rest, l->stream);
       if (e != cudaSuccess) return cuda_fail(l, e, "boundary kernel launch");
     }
     l->cur ^= 1;

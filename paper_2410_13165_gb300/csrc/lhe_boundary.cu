@@ -20,8 +20,10 @@
 // folded into U and V). Full-way: f_k = omega_k [h(x) - C_k - sum_m T_mk cos xi_m]; half-way:
 // f_k = wp_k lin(x) + K_k + sum_m (U_mk sin xi_m + V_mk cos xi_m) - f*_kbar(x), lin = linear part of h.
 // The phase xi_m at a node is assembled from tabulated per-axis factors; boundary nodes come
-// grouped by face signature so that a warp shares one set of unknown populations.
-#include "lhe_internal.h"
+// grouped by face signature so that a warp shares one set of unknown populations. The per-node
+// evaluation (lhe_bnode.cuh) is shared with the FP64 interior kernel of Dirichlet boxes, which treats
+// the nodes of the two x_1 faces (whose other coordinates are interior) in the lanes of their rows.
+#include "lhe_bnode.cuh"
 
 namespace lhe {
 
@@ -47,35 +49,8 @@ __global__ void __launch_bounds__(128) k_boundary(const BoundaryArgs a) {
       }
     }
   }
-  double X[D];
-#pragma unroll
-  for (int i = 0; i < D; ++i) X[i] = a.x0[i] + (double)x[i] * a.dx;
-  const double te = a.t_eval;
-  const int M = a.nmodes;
-  // (cos, sin) of xi_m = theta_m - kappa_m . u t + sum_i kappa_mi X_i: the step's time factor times the
-  // node's per-axis factors (tabulated on the host), with no transcendental call per node.
-  double sn[kMaxModes], cs[kMaxModes];
-  for (int m = 0; m < M; ++m) {
-    double c = a.ph_c[m], s = a.ph_s[m];
-#pragma unroll
-    for (int i = 0; i < D; ++i) {
-      const double *t = a.axis + 2 * ((size_t)m * a.axis_len + a.axis_off[i] + x[i]);
-      const double ca = __ldg(t), sa = __ldg(t + 1);
-      const double c2 = fma(c, ca, -s * sa);
-      s = fma(c, sa, s * ca);
-      c = c2;
-    }
-    sn[m] = s;
-    cs[m] = c;
-  }
-  double lin0 = a.b + a.R * te;  // linear part of h at (x, t_eval)
-#pragma unroll
-  for (int i = 0; i < D; ++i) lin0 = fma(a.gl[i], X[i] - a.u[i] * te, lin0);
-  const double *coef = a.table;                                 // [m][k][2]
-  const double *kconst = a.table + (size_t)2 * a.nmodes * Q;    // [k][2]
-  double H = lin0;  // h(x, t_eval) (full-way)
-  if (KIND == 1)
-    for (int m = 0; m < M; ++m) H = fma(a.a[m], sn[m], H);
+  BNode<D> nd;
+  bnode_prepare<D, KIND>(a, x, nd);
 
   const double *__restrict__ fsrc = static_cast<const double *>(a.src);
   const float *__restrict__ gsrc = static_cast<const float *>(a.src);
@@ -96,21 +71,7 @@ __global__ void __launch_bounds__(128) k_boundary(const BoundaryArgs a) {
       v[k] = DEV ? fma(a.omega[k], df_value(a.phi_src[o]), (double)gsrc[k * S + o]) : fsrc[k * S + o];
       continue;
     }
-    if (KIND == 1) {
-      double acc = H - __ldg(kconst + 2 * k);
-      for (int m = 0; m < M; ++m) acc = fma(-__ldg(coef + 2 * (m * Q + k)), cs[m], acc);
-      v[k] = a.omega[k] * acc;
-    } else {
-      const int kb = L.opp[k];
-      double acc = fma(__ldg(kconst + 2 * k), lin0, __ldg(kconst + 2 * k + 1));
-      for (int m = 0; m < M; ++m) {
-        acc = fma(__ldg(coef + 2 * (m * Q + k)), sn[m], acc);
-        acc = fma(__ldg(coef + 2 * (m * Q + k) + 1), cs[m], acc);
-      }
-      const double fkb = DEV ? fma(a.omega[kb], df_value(a.phi_src[site]), (double)gsrc[kb * S + site])
-                              : fsrc[kb * S + site];
-      v[k] = acc - fkb;
-    }
+    v[k] = bnode_unknown<D, KIND, DEV>(a, nd, k, site);
   }
   // collision, as in the bulk: phi = sum_k f_k (fixed-point sum), f*_k = (1 - s) f_k + omega_k (s phi + dt R)
   const double phi = fixed_moment_sum<Q, 0>(v);

@@ -161,6 +161,8 @@ struct AdjGradArgs {
 cudaError_t launch_step_fp64(int d, bool adjoint, bool interior, const StepArgs &a, cudaStream_t st);
 cudaError_t launch_step_dev(int d, bool adjoint, bool interior, const StepArgs &a, cudaStream_t st);
 cudaError_t launch_boundary(int d, int kind, bool dev, const BoundaryArgs &a, cudaStream_t st);
+cudaError_t launch_step_box_fp64(int d, int kind, const StepArgs &a, const BoundaryArgs &b, double *xb, int64_t nrows,
+                                 cudaStream_t st);
 cudaError_t launch_adjoint_boundary(int d, int kind, const BoundaryArgs &a, cudaStream_t st);
 cudaError_t launch_stability(int d, const double *omega_dev, int64_t npoints, int32_t nxi, double s,
                              unsigned long long *rho_bits_dev, cudaStream_t st);
@@ -208,6 +210,9 @@ struct lhe_lbm {
   // Dirichlet
   int32_t *bsites = nullptr;
   int64_t nb = 0;
+  int64_t nb_xface = 0;         // leading entries of bsites on the x_1 faces only (other coordinates
+                                // interior): the FP64 forward step treats them in the row kernel
+  double *xface = nullptr;      // their boundary data per step (2 (2d - 1) doubles per interior row)
   bool have_wave = false;
   lhe_wave wave{};
   double *bc_table = nullptr;

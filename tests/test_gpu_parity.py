@@ -175,6 +175,21 @@ def test_fp64_dirichlet_d4q33_12(bc, u):
     assert relerr(g, o) < FP64_TOL
 
 
+@pytest.mark.parametrize("bc", ["fullway", "halfway"])
+@pytest.mark.parametrize("d,n,u,tau", [
+    (1, (23,), (0.3,), 0.5), (1, (16,), (0.1,), 0.8),
+    (2, (3, 17), (0.1, 0.05), 0.8), (3, (9, 6, 7), (0.1, -0.05, 0.08), 1.2),
+    (5, (5, 4, 6, 5, 4), (0.02, 0.04, 0.06, 0.08, 0.1), 0.5), (5, (4, 5, 4, 4, 5), (0.01,) * 5, 0.8)])
+def test_fp64_dirichlet_all_dimensions(bc, d, n, u, tau):
+    """Both Dirichlet schemes in d = 1..5 on ragged boxes (including rows of 3 nodes), with the
+    s = 2 and the general collision: the x_1-face nodes go through the interior-row kernel, the
+    other boundary nodes through the boundary-node kernel."""
+    h = 1.0 / 16
+    hi = [(ni - 1) * h if bc == "fullway" else ni * h for ni in n]
+    g, o = run_pair(d, n, u, 20, hi=hi, tau=tau, R=0.6, bc=bc, nmodes=2, seed=31 + d)
+    assert rel(g, o) < FP64_TOL
+
+
 # ------------------------------------------------------------------------------ FP32 deviations
 
 def test_fp32dev_d3q19_periodic():

@@ -21,8 +21,15 @@
 
 namespace lhe {
 
+// Register caps for the large lattices: D4Q33 at 5 resident blocks per SM (96 registers, no spills)
+// and D5Q51 at 4 (128 registers instead of 146, 16 bytes spilled) keep more loads in flight per SM;
+// measured 71 -> 87 % and 66 -> 74 % of the HBM bandwidth (D4Q33 48^4, D5Q51 24^5). The FP64 kernel
+// is not capped: there the spills cost more than the occupancy gains (D5Q51 76 -> 66 %).
+template <int D>
+constexpr int dev_min_blocks() { return D == 4 ? 5 : (D == 5 ? 4 : 1); }
+
 template <int D, bool ADJ, bool INTERIOR, bool S2>
-__global__ void __launch_bounds__(LHE_STEP_THREADS) k_step_dev(const StepArgs a) {
+__global__ void __launch_bounds__(LHE_STEP_THREADS, dev_min_blocks<D>()) k_step_dev(const StepArgs a) {
   constexpr Lattice<D> L{};
   constexpr int Q = Lattice<D>::Q;
   pdl_trigger();

@@ -44,7 +44,8 @@ def _problem(d, n, seed):
 
 
 @pytest.mark.parametrize("tau", [0.5, 0.8])
-@pytest.mark.parametrize("d,n,u", [(2, 8, (0.1, -0.2)), (3, 6, (0.1, 0.05, -0.15)), (1, 12, (0.3,))])
+@pytest.mark.parametrize("d,n,u", [(2, 8, (0.1, -0.2)), (3, 6, (0.1, 0.05, -0.15)), (1, 12, (0.3,)),
+                                   (4, 5, (0.05, 0.1, 0.08, 0.1)), (5, 4, (0.02, 0.04, 0.06, 0.08, 0.1))])
 @pytest.mark.parametrize("order,explicit", [(3, False), (3, True), (1, False)])
 def test_fp64_adjoint_matches_the_oracle(d, n, u, tau, order, explicit):
     phi0, R, target = _problem(d, n, 40 + d)

@@ -89,6 +89,17 @@ def test_fp64_periodic_ragged_extents_all_dimensions(d, n):
     assert rel(g, o) < FP64_TOL
 
 
+@pytest.mark.parametrize("tau", [0.5, 0.8, 1.2])
+def test_fp64_d5q51_source_field(tau):
+    """D5Q51 (two lanes per node on the GPU) with a per-site source field, each collision form."""
+    n = (6, 5, 4, 5, 6)
+    S = int(np.prod(n))
+    Rf = 0.4 * np.random.default_rng(15).normal(size=S)
+    g, o = run_pair(5, n, (0.02, 0.04, 0.06, 0.08, 0.1), 12, hi=[ni / 16.0 for ni in n], tau=tau, Rfield=Rf,
+                    nmodes=3, seed=16)
+    assert rel(g, o) < FP64_TOL
+
+
 def test_fp64_d3q19_64cubed_1000_steps():
     """D3Q19 64^3, 8 modes, 1000 steps (the parity case of the 256^3 workload's family)."""
     g, o = run_pair(3, 64, (0.1, 0.1, 0.1), 1000, tau=0.5, nmodes=8, seed=2)

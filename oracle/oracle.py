@@ -274,6 +274,83 @@ class Model:
             cur, nxt = nxt, cur
         return cur
 
+    def step_jets(self, f, n0, nsteps, jet_fn) -> np.ndarray:
+        """Dirichlet steps with the boundary data given as jets of phi: jet_fn(points (P, d), t)
+        returns (P, J) arrays of every derivative of order 0..3 in (t, x_1..x_d), ordered by length
+        and then lexicographically over non-decreasing variable tuples (0: t, i: x_i). The unknown
+        populations follow Eq. (bun1) (at the node, t + dt) and Eq. (bun2) (at x - c_k dt/2, t) with
+        the directional derivatives d_t^q (c . grad)^p phi formed from the jets, term by term as in
+        boundary_value of lhe_oracle.c."""
+        if self.bc == "periodic":
+            raise ValueError("jets are Dirichlet data")
+        import itertools
+
+        d, S, Q = self.d, self.S, self.Q
+        pos, j = {}, 0
+        for q in range(4):
+            for tup in itertools.combinations_with_replacement(range(d + 1), q):
+                pos[tup] = j
+                j += 1
+        X = self.coords()
+        idx = np.stack(np.unravel_index(np.arange(S), self.n[::-1])[::-1])  # (d, S), x_1 fastest
+        sites, links = [], []
+        for site in range(S):
+            for k in range(Q):
+                src = idx[:, site] - self.e[k]
+                if np.any(src < 0) or np.any(src >= np.asarray(self.n)):
+                    sites.append(site)
+                    links.append(k)
+        sites, links = np.asarray(sites, dtype=np.int64), np.asarray(links, dtype=np.int64)
+        ck = self.c * self.e[links].astype(np.float64)      # (U, d)
+        dt = self.dt
+        kb = np.array([int(np.nonzero(np.all(self.e == -self.e[k], axis=1))[0][0]) for k in links], dtype=np.int64)
+        wk, wkb = self.omega[links], self.omega[kb]
+
+        def dir_deriv(J, p, q):
+            """d_t^q (c_k . grad)^p phi from the jets J (U, J), summed over ordered spatial tuples."""
+            out = np.zeros(len(links))
+            for sp in itertools.product(range(1, d + 1), repeat=p):
+                w = np.ones(len(links))
+                for i in sp:
+                    w = w * ck[:, i - 1]
+                out += w * J[:, pos[tuple(sorted((0,) * q + sp))]]
+            return out
+
+        w = OrcWave()  # no wave data: the unknown populations are replaced below
+        cur = np.ascontiguousarray(f, dtype=np.float64).copy()
+        star = np.empty_like(cur)
+        nxt = np.empty_like(cur)
+        L = lib()
+        for n in range(n0, n0 + nsteps):
+            L.orc_step(ctypes.byref(self._m), ctypes.byref(w), n, None, _p(cur), _p(star), _p(nxt))
+            if self.bc == "fullway":
+                t1 = (n + 1) * dt
+                J = np.asarray(jet_fn(X[:, sites].T.copy(), t1), dtype=np.float64)
+                feq = wk * dir_deriv(J, 0, 0)
+                if self.bc_order == 1:
+                    val = feq
+                else:
+                    val = feq - 0.5 * dt * wk * dir_deriv(J, 1, 0) - 0.5 * dt * wk * dir_deriv(J, 0, 1) + 0.5 * dt * wk * self.R
+                    if self.bc_order >= 4:
+                        val = val + dt ** 3 / 8.0 * wk * dir_deriv(J, 1, 2) + dt ** 3 / 8.0 * wk * dir_deriv(J, 2, 1) \
+                            + dt ** 3 / 24.0 * wk * dir_deriv(J, 0, 3) + dt ** 3 / 24.0 * wk * dir_deriv(J, 3, 0)
+            else:
+                t0 = n * dt
+                J = np.asarray(jet_fn((X[:, sites].T - 0.5 * dt * ck).copy(), t0), dtype=np.float64)
+                wsum, wdif = wk + wkb, wk - wkb
+                B = wsum * dir_deriv(J, 0, 0)
+                if self.bc_order >= 2:
+                    B = B + 0.5 * dt * wsum * dir_deriv(J, 0, 1) + 0.5 * dt * (wk * self.R + wkb * self.R)
+                if self.bc_order >= 3:
+                    B = B - dt * dt / 8.0 * wsum * dir_deriv(J, 2, 0) - dt * dt / 4.0 * wdif * dir_deriv(J, 1, 1)
+                if self.bc_order >= 4:
+                    B = B - dt ** 3 / 8.0 * wdif * dir_deriv(J, 1, 2) - dt ** 3 / 16.0 * wsum * dir_deriv(J, 2, 1) \
+                        - dt ** 3 / 24.0 * wsum * dir_deriv(J, 0, 3)
+                val = -star[kb, sites] + B
+            nxt[links, sites] = val
+            cur, nxt = nxt, cur
+        return cur
+
     def phi(self, f) -> np.ndarray:
         out = np.empty(self.S)
         lib().orc_phi(ctypes.byref(self._m), _p(np.ascontiguousarray(f)), _p(out))

@@ -140,3 +140,92 @@ def tanh_bubble(X: np.ndarray, t: float, u, lo, hi):
     with np.errstate(invalid="ignore", divide="ignore"):
         grad = np.where(r > 0, dval_dr * Y / np.where(r > 0, r, 1.0), 0.0)
     return val, grad
+
+
+# ---- boundary data as jets (every derivative of order 0..3 in (t, x_1..x_d) at given points) ----
+
+def _jet_tuples(d: int):
+    """Variable tuples of a jet (0: t, i: x_i): lengths 0..3, non-decreasing, lexicographic."""
+    import itertools
+
+    return [tup for q in range(4) for tup in itertools.combinations_with_replacement(range(d + 1), q)]
+
+
+def wave_jets(points: np.ndarray, t: float, u, R: float, a, kappa, theta, b: float = 0.0, g=None) -> np.ndarray:
+    """Jets of h = b + R t + g.(x - u t) + sum_m a_m sin(kappa_m.(x - u t) + theta_m) at points (P, d):
+    a derivative over x_i contributes kappa_mi, one over t contributes -kappa_m.u, to the m-th mode."""
+    P, d = points.shape
+    u = np.asarray(u, dtype=np.float64)
+    g = np.zeros(d) if g is None else np.asarray(g, dtype=np.float64)
+    tuples = _jet_tuples(d)
+    out = np.zeros((P, len(tuples)))
+    Y = points - u[None, :] * t
+    for col, tup in enumerate(tuples):
+        if len(tup) == 0:
+            out[:, col] = b + R * t + Y @ g
+        elif len(tup) == 1:
+            out[:, col] = (R - g @ u) if tup[0] == 0 else g[tup[0] - 1]
+        for m in range(len(a)):
+            km = np.asarray(kappa[m], dtype=np.float64)
+            fac = a[m]
+            for v in tup:
+                fac *= -(km @ u) if v == 0 else km[v - 1]
+            xi = Y @ km + theta[m]
+            out[:, col] += fac * [np.sin, np.cos, lambda z: -np.sin(z), lambda z: -np.cos(z)][len(tup) % 4](xi)
+    return out
+
+
+def gaussian_jets(points: np.ndarray, t: float, u, R: float, A: float, xc, sigma: float) -> np.ndarray:
+    """Jets of phi = A exp(-|x - u t - xc|^2 / (2 sigma^2)) + R t, an exact solution of
+    phi_t + u.grad phi = R that the sine family does not contain. A derivative over t acts on the pulse
+    as -u.grad."""
+    import itertools
+
+    P, d = points.shape
+    u = np.asarray(u, dtype=np.float64)
+    Y = points - u[None, :] * t - np.asarray(xc, dtype=np.float64)[None, :]
+    s2 = sigma * sigma
+    G = A * np.exp(-np.sum(Y * Y, axis=1) / (2.0 * s2))
+
+    def spatial(idx):  # derivative of the pulse over the spatial indices idx (0-based), order <= 3
+        if len(idx) == 0:
+            return G
+        if len(idx) == 1:
+            i, = idx
+            return -Y[:, i] / s2 * G
+        if len(idx) == 2:
+            i, j = idx
+            return (Y[:, i] * Y[:, j] / s2 ** 2 - (1.0 if i == j else 0.0) / s2) * G
+        i, j, k = idx
+        return (-Y[:, i] * Y[:, j] * Y[:, k] / s2 ** 3
+                + ((i == j) * Y[:, k] + (i == k) * Y[:, j] + (j == k) * Y[:, i]) / s2 ** 2) * G
+
+    tuples = _jet_tuples(d)
+    out = np.zeros((P, len(tuples)))
+    for col, tup in enumerate(tuples):
+        nt = sum(1 for v in tup if v == 0)
+        sp = [v - 1 for v in tup if v != 0]
+        acc = np.zeros(P)
+        for ls in itertools.product(range(d), repeat=nt):  # (-u.grad)^nt
+            w = 1.0
+            for l in ls:
+                w *= -u[l]
+            acc += w * spatial(sp + list(ls))
+        out[:, col] = acc
+        if len(tup) == 0:
+            out[:, col] += R * t
+        elif tup == (0,):
+            out[:, col] += R
+    return out
+
+
+def gaussian_value(X: np.ndarray, t: float, u, R: float, A: float, xc, sigma: float) -> np.ndarray:
+    """The pulse solution at nodes X (d, S)."""
+    Y = X - np.asarray(u, dtype=np.float64)[:, None] * t - np.asarray(xc, dtype=np.float64)[:, None]
+    return A * np.exp(-np.sum(Y * Y, axis=0) / (2.0 * sigma * sigma)) + R * t
+
+
+def gaussian_grad(X: np.ndarray, t: float, u, A: float, xc, sigma: float) -> np.ndarray:
+    Y = X - np.asarray(u, dtype=np.float64)[:, None] * t - np.asarray(xc, dtype=np.float64)[:, None]
+    G = A * np.exp(-np.sum(Y * Y, axis=0) / (2.0 * sigma * sigma))
+    return -Y / (sigma * sigma) * G[None, :]

@@ -1,0 +1,54 @@
+"""Oracle: Dirichlet data given as jets of phi (CPU).
+
+Pins of the jet path of the oracle (Model.step_jets): fed the jets of the exact-solution family it
+must reproduce the family's own path (orc_step with the wave, pinned elsewhere), every boundary order
+of both schemes; fed a Gaussian pulse, an exact solution of Eq. (HE) outside the family, the
+fourth-order schemes converge at rate ~4 (Table 1's rates; Eq. (cr-estimation): Z = min(K+1, P))."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2410_13165_gb300 import workloads as W
+
+
+def _wave_case(d, bc, n, u, order, tau=0.5, R=0.6):
+    h = 1.0 / 16
+    hi = [(n - 1) * h if bc == "fullway" else n * h] * d
+    m = O.Model(d, [n] * d, 0.0, hi, u, tau=tau, R=R, bc=bc, bc_order=order)
+    F = W.fourier_field(d, 2, 50 + d, 0.0, hi)
+    a, kap, th = F.wave_params()
+    X = m.coords()
+    f0 = m.init(F.value(X), F.grad(X), 3)
+    return m, F, a, kap, th, f0
+
+
+@pytest.mark.parametrize("bc,order", [("fullway", 1), ("fullway", 3), ("fullway", 4), ("halfway", 1), ("halfway", 2),
+                                      ("halfway", 3), ("halfway", 4)])
+@pytest.mark.parametrize("d", [2, 3])
+def test_jets_of_the_wave_family_reproduce_the_wave_path(d, bc, order):
+    u = (0.1, 0.05, -0.08)[:d] if bc == "fullway" else (0.01, 0.02, -0.01)[:d]
+    m, F, a, kap, th, f0 = _wave_case(d, bc, 9 if d == 2 else 6, u, order, tau=0.8 if order == 3 else 0.5)
+    w = m.wave(a=a, kappa=kap, theta=th, b=0.3, g=[0.2, -0.1, 0.4][:d])
+    ref = m.step(f0, 0, 7, wave=w)
+    jets = lambda P, t: W.wave_jets(P, t, u, m.R, a, kap, th, 0.3, [0.2, -0.1, 0.4][:d])
+    got = m.step_jets(f0, 0, 7, jets)
+    assert np.max(np.abs(got - ref)) < 1e-13 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("bc,u", [("fullway", (0.1, 0.05)), ("halfway", (0.01, 0.02))])
+def test_gaussian_pulse_converges_at_fourth_order(bc, u):
+    """phi = exp(-|x - u t - xc|^2 / (2 sigma^2)) + R t on [0, 1]^2, boundary data from its jets,
+    K = 3 initialisation, T = 0.5: the RMSE against the exact pulse falls at rate ~4."""
+    R, A, xc, sig, T = 0.5, 1.0, (0.45, 0.55), 0.18, 0.5
+    errs = []
+    for N in (16, 32, 64):
+        n = N + 1 if bc == "fullway" else N
+        m = O.Model(2, n, 0.0, 1.0, u, R=R, bc=bc)
+        X = m.coords()
+        f = m.init(W.gaussian_value(X, 0.0, u, R, A, xc, sig), W.gaussian_grad(X, 0.0, u, A, xc, sig), 3)
+        steps = int(round(T / m.dt))
+        f = m.step_jets(f, 0, steps, lambda P, t: W.gaussian_jets(P, t, u, R, A, xc, sig))
+        exact = W.gaussian_value(X, steps * m.dt, u, R, A, xc, sig)
+        errs.append(float(np.sqrt(np.mean((m.phi(f) - exact) ** 2))))
+    rates = [np.log2(a / b) for a, b in zip(errs, errs[1:])]
+    assert 3.5 < rates[-1] < 4.6, (errs, rates)

@@ -180,9 +180,38 @@ LHE_API lhe_status lhe_lbm_init(lhe_lbm *lbm, const double *phi0_dev, const doub
 /* Set the Dirichlet data (copied). Required before lhe_lbm_step on a full-way or half-way box. */
 LHE_API lhe_status lhe_lbm_set_boundary_wave(lhe_lbm *lbm, const lhe_wave *w_host);
 
+/* Number of values in a boundary jet: every derivative of phi of order 0..3 in the d + 1 variables
+ * (t, x_1, ..., x_d), C(d + 4, 3) = 10, 20, 35, 56, 84 for d = 1..5. */
+#define LHE_JET_LEN(d) (((d) + 4) * ((d) + 3) * ((d) + 2) / 6)
+
+/* Points at which lhe_lbm_set_boundary_jet needs the Dirichlet data of the next step (Sec. 3.2):
+ *   full-way (Eq. (bun1)): the boundary nodes, data at the new time t_{n+1};
+ *   half-way (Eq. (bun2)): for every boundary node x_f and unknown population k (source x_f - e_k
+ *     outside the box), the mid-link point x_f - c_k dt/2, data at the current time t_n.
+ * Nodes come in the library's boundary-node order; half-way, a node's unknown links in the order of
+ * k. *P_host receives the number of points; xyz_host (host, P*d doubles, point-major) receives the
+ * coordinates, or is NULL to query P only; *t_offset_host (or NULL) receives the time of the data
+ * minus t_n (dt full-way, 0 half-way), with t_n = info.step * dt. Errors: LHE_ERR_STATE on a
+ * periodic box, LHE_ERR_ARG when P_host is NULL. */
+LHE_API lhe_status lhe_lbm_boundary_points(const lhe_lbm *lbm, double *xyz_host, int64_t *P_host, double *t_offset_host);
+
+/* Dirichlet data of the next step as jets of phi at the points of lhe_lbm_boundary_points, for
+ * data that the exact-solution family of lhe_lbm_set_boundary_wave does not cover. jet_dev (device,
+ * P * LHE_JET_LEN(d) doubles, point-major) holds at each point every derivative d^q phi / (dv_1 ..
+ * dv_q), q = 0..3, over the non-decreasing tuples v_1 <= .. <= v_q of the variables (v = 0: t, v = i:
+ * x_i), tuples of one length in lexicographic order: phi, phi_t, phi_x1, .., phi_tt, phi_tx1, ...
+ * The library forms the unknown populations of Eq. (bun1) (orders 1, 3, 4) or the B_k of Eq. (bun2)
+ * (orders 1..4) from them, asynchronously on the handle's stream (jet_dev must stay valid until the
+ * stream has passed this call). The data serve exactly one step: the next lhe_lbm_step must have
+ * n = 1 and needs new jets after it (LHE_ERR_STATE otherwise). lhe_lbm_set_boundary_wave switches
+ * back to the exact-solution family. The constant R of the box enters as in the family's case.
+ * Errors: LHE_ERR_STATE on a periodic box, LHE_ERR_ARG for NULL, LHE_ERR_CUDA. */
+LHE_API lhe_status lhe_lbm_set_boundary_jet(lhe_lbm *lbm, const double *jet_dev);
+
 /* Advance n >= 0 time steps of Eq. (BGK-LB-Evolution) (collide with s = 1/tau, stream), with
  * the full-way (Eq. (bun1)) or half-way (Eq. (bun2)) scheme for the unknown populations of the
- * boundary nodes of a Dirichlet box. Errors: LHE_ERR_STATE before init / without boundary data. */
+ * boundary nodes of a Dirichlet box. Errors: LHE_ERR_STATE before init / without boundary data, and
+ * with boundary jets when n > 1 or no jets were set since the last step. */
 LHE_API lhe_status lhe_lbm_step(lhe_lbm *lbm, int64_t n);
 
 /* Macroscopic variable phi(x, t_step) = sum_k f_k (Eq. (0-1-meq)) into phi_dev (S doubles). */

@@ -49,6 +49,19 @@ def _params(d, n, lo=0.0, hi=1.0, u=None, R=0.0, tau=0.5, c=1.0, bc="periodic", 
     return p
 
 
+def jet_len(d: int) -> int:
+    """Number of derivatives in a boundary jet: orders 0..3 in the d + 1 variables (t, x_1..x_d)."""
+    return (d + 4) * (d + 3) * (d + 2) // 6
+
+
+def jet_index(d: int):
+    """The derivatives of a boundary jet, in order: tuples of variable indices (0: t, i: x_i),
+    non-decreasing, of length 0..3, lexicographic within each length."""
+    import itertools
+
+    return [tup for q in range(4) for tup in itertools.combinations_with_replacement(range(d + 1), q)]
+
+
 def model(d, u, c=1.0, g=0.5, m4=None, allow_unstable=False):
     """EDF weights omega_k, fourth moments and lattice vectors as computed by the library."""
     p = _params(d, 4, u=u, c=c, g=g, m4=m4)
@@ -134,6 +147,19 @@ class LBM:
                 w.kappa[m * _abi.MAX_DIM + i] = float(kappa[m][i])
         self._stream()
         _abi.lhe_lbm_set_boundary_wave(self.h, w)
+
+    def boundary_points(self):
+        """(points[P][d] as a numpy array, t_offset): the points where the Dirichlet jets of the next
+        step are needed (full-way: the boundary nodes; half-way: the mid-link points of the unknown
+        populations) and the time of those data relative to the current time step_index * dt."""
+        return _abi.lhe_lbm_boundary_points(self.h, self.d)
+
+    def set_boundary_jet(self, jet):
+        """Jets of phi at boundary_points() for the next step: a float64 tensor of P * jet_len(d)
+        values (every derivative of order 0..3 in (t, x_1..x_d), in the order of jet_index(d))."""
+        P = len(self.boundary_points()[0])
+        self._stream()
+        _abi.lhe_lbm_set_boundary_jet(self.h, self._ptr(jet, P * jet_len(self.d), "jet"))
 
     def step(self, n: int = 1):
         self._stream()

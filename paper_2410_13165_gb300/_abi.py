@@ -30,7 +30,7 @@ EXPORTS = [
     "lhe_lbm_destroy", "lhe_lbm_last_error", "lhe_lbm_info", "lhe_lbm_set_stream", "lhe_lbm_init",
     "lhe_lbm_set_boundary_wave", "lhe_lbm_step", "lhe_lbm_macro", "lhe_lbm_diagnostics", "lhe_lbm_get_state",
     "lhe_lbm_set_state", "lhe_lbm_adjoint_seed", "lhe_lbm_adjoint_step", "lhe_lbm_adjoint_grads",
-    "lhe_lbm_diagnostics_noalloc", "lhe_lbm_stability_map",
+    "lhe_lbm_diagnostics_noalloc", "lhe_lbm_stability_map", "lhe_lbm_boundary_points", "lhe_lbm_set_boundary_jet",
 ]
 
 
@@ -98,6 +98,8 @@ def load(path: str | None = None):
         "lhe_lbm_set_stream": (st, [_H, ctypes.c_void_p]),
         "lhe_lbm_init": (st, [_H, _D, _D, _D]),
         "lhe_lbm_set_boundary_wave": (st, [_H, ctypes.POINTER(lhe_wave)]),
+        "lhe_lbm_boundary_points": (st, [_H, _D, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double)]),
+        "lhe_lbm_set_boundary_jet": (st, [_H, _D]),
         "lhe_lbm_step": (st, [_H, ctypes.c_int64]),
         "lhe_lbm_macro": (st, [_H, _D]),
         "lhe_lbm_diagnostics": (st, [_H, ctypes.POINTER(ctypes.c_double)]),
@@ -176,6 +178,25 @@ def lhe_lbm_init(h, phi0_ptr: int, grad_ptr: int | None, R_ptr: int | None) -> N
 
 def lhe_lbm_set_boundary_wave(h, w: lhe_wave) -> None:
     check(load().lhe_lbm_set_boundary_wave(h, ctypes.byref(w)), h)
+
+
+def lhe_lbm_boundary_points(h, d: int):
+    """(points[P][d], t_offset): where the Dirichlet jets of the next step are needed and the time of
+    the data relative to the current step's time."""
+    import numpy as np
+
+    L = load()
+    P = ctypes.c_int64(0)
+    toff = ctypes.c_double(0.0)
+    check(L.lhe_lbm_boundary_points(h, None, ctypes.byref(P), ctypes.byref(toff)), h)
+    pts = np.zeros((P.value, d), dtype=np.float64)
+    if P.value:
+        check(L.lhe_lbm_boundary_points(h, pts.ctypes.data, ctypes.byref(P), ctypes.byref(toff)), h)
+    return pts, toff.value
+
+
+def lhe_lbm_set_boundary_jet(h, jet_ptr: int) -> None:
+    check(load().lhe_lbm_set_boundary_jet(h, jet_ptr), h)
 
 
 def lhe_lbm_step(h, n: int) -> None:

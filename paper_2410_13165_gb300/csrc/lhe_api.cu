@@ -402,6 +402,27 @@ lhe_status lhe_lbm_create(const lhe_lbm_params *p, lhe_lbm **out) {
       if (keyed[j].first <= 2) ++l->nb_xface;  // signatures 1 and 2 (x_1 face only) sort first
     }
     l->nb = (int64_t)sites.size();
+    // records of boundary data given as jets: one per (boundary node, unknown link), in node order
+    l->bsites_host = sites;
+    l->broff_host.resize(sites.size());
+    int64_t nrec = 0;
+    for (size_t j = 0; j < sites.size(); ++j) {
+      l->broff_host[j] = (int32_t)nrec;
+      int32_t w = keyed[j].first;
+      int unknown_links = 0;
+      for (int k = 0; k < m.Q; ++k) {
+        bool unknown = false;
+        int32_t ws = w;
+        for (int i = 0; i < p->d; ++i, ws /= 3) {
+          const int e_ki = m.e[k * p->d + i];
+          if ((ws % 3 == 1 && e_ki == 1) || (ws % 3 == 2 && e_ki == -1)) unknown = true;
+        }
+        unknown_links += unknown ? 1 : 0;
+      }
+      nrec += unknown_links;
+      if (nrec > 0x7fffffff) return bail(fail(l, LHE_ERR_ARG, "too many boundary records"));
+    }
+    l->nrec = nrec;
     if (p->precision == LHE_FP64) {
       const int64_t nrows = l->g.S_rows / l->g.n[0];
       e = cudaMalloc(&l->xface, sizeof(double) * (size_t)(2 * nrows * (2 * p->d - 1)));
@@ -450,6 +471,8 @@ lhe_status lhe_lbm_destroy(lhe_lbm *l) {
   cudaFree(l->Rfield);
   cudaFree(l->fdgrad);
   cudaFree(l->bsites);
+  cudaFree(l->broff);
+  cudaFree(l->brec);
   cudaFree(l->xface);
   cudaFree(l->bc_table);
   cudaFree(l->bc_axis);
@@ -619,8 +642,11 @@ lhe_status lhe_lbm_set_boundary_wave(lhe_lbm *l, const lhe_wave *w) {
   if (!ax.empty()) LHE_CK(l, cudaMemcpy(l->bc_axis, ax.data(), sizeof(double) * ax.size(), cudaMemcpyHostToDevice));
   l->wave = *w;
   l->have_wave = true;
+  l->jet_mode = false;
+  l->jet_ready = false;
   return LHE_OK;
 }
+
 
 static BoundaryArgs boundary_args(const lhe_lbm *l) {
   BoundaryArgs b{};
@@ -666,13 +692,93 @@ static BoundaryArgs boundary_args(const lhe_lbm *l) {
   return b;
 }
 
+lhe_status lhe_lbm_boundary_points(const lhe_lbm *l, double *xyz_host, int64_t *P, double *t_offset) {
+  if (!l) return fail(nullptr, LHE_ERR_ARG, "handle is NULL");
+  lhe_lbm *lm = const_cast<lhe_lbm *>(l);
+  if (!P) return fail(lm, LHE_ERR_ARG, "P is NULL");
+  if (l->p.bc == LHE_BC_PERIODIC) return fail(lm, LHE_ERR_STATE, "boundary points of a periodic box");
+  const int d = l->p.d;
+  const bool full = l->p.bc == LHE_BC_FULLWAY;
+  *P = full ? l->nb : l->nrec;
+  if (t_offset) *t_offset = full ? l->dt : 0.0;
+  if (!xyz_host) return LHE_OK;
+  int64_t q = 0;
+  for (size_t j = 0; j < l->bsites_host.size(); ++j) {
+    int64_t r = l->bsites_host[j];
+    int64_t idx[kMaxD];
+    double x[kMaxD];
+    for (int i = 0; i < d; ++i) {
+      idx[i] = r % l->p.n[i];
+      r /= l->p.n[i];
+      x[i] = l->x0[i] + (double)idx[i] * l->dx;
+    }
+    if (full) {
+      for (int i = 0; i < d; ++i) xyz_host[q * d + i] = x[i];
+      ++q;
+      continue;
+    }
+    for (int k = 0; k < l->Q; ++k) {  // half-way: the mid-link point x - e_k dx/2 of every unknown link
+      bool unknown = false;
+      for (int i = 0; i < d; ++i) {
+        const int64_t src = idx[i] - l->e[k * d + i];
+        if (src < 0 || src >= l->p.n[i]) unknown = true;
+      }
+      if (!unknown) continue;
+      for (int i = 0; i < d; ++i) xyz_host[q * d + i] = x[i] - 0.5 * l->dx * l->e[k * d + i];
+      ++q;
+    }
+  }
+  return LHE_OK;
+}
+
+lhe_status lhe_lbm_set_boundary_jet(lhe_lbm *l, const double *jet_dev) {
+  if (lhe_status s = check_handle(l)) return s;
+  if (l->p.bc == LHE_BC_PERIODIC) return fail(l, LHE_ERR_STATE, "boundary data on a periodic box");
+  if (!jet_dev) return fail(l, LHE_ERR_ARG, "jet is NULL");
+  if (lhe_status st = check_pipeline(l)) return st;
+  const int d = l->p.d;
+  if (!l->broff) {
+    LHE_CK(l, cudaMalloc((void **)&l->broff, sizeof(int32_t) * l->broff_host.size()));
+    LHE_CK(l, cudaMemcpy(l->broff, l->broff_host.data(), sizeof(int32_t) * l->broff_host.size(), cudaMemcpyHostToDevice));
+    LHE_CK(l, cudaMalloc((void **)&l->brec, sizeof(double) * (size_t)std::max<int64_t>(l->nrec, 1)));
+  }
+  // position of each derivative in a jet: orders 0..3, index tuples v1 <= .. <= vq in lexicographic
+  // order (v = 0: t, v = i: x_i); the tables list every ordering of a tuple
+  std::vector<int16_t> jidx(216 + 36, 0);
+  int16_t pos = (int16_t)(1 + (d + 1));
+  for (int a = 0; a <= d; ++a)
+    for (int b = a; b <= d; ++b) {
+      jidx[216 + a * 6 + b] = pos;
+      jidx[216 + b * 6 + a] = pos;
+      ++pos;
+    }
+  for (int a = 0; a <= d; ++a)
+    for (int b = a; b <= d; ++b)
+      for (int c = b; c <= d; ++c) {
+        const int perm[6][3] = {{a, b, c}, {a, c, b}, {b, a, c}, {b, c, a}, {c, a, b}, {c, b, a}};
+        for (const auto &q : perm) jidx[q[0] * 36 + q[1] * 6 + q[2]] = pos;
+        ++pos;
+      }
+  BoundaryArgs b = boundary_args(l);
+  b.roff = l->broff;  // the kernel writes l->brec; b.rec stays null (the data are being formed)
+  LHE_CK(l, launch_jet_records(d, l->p.bc, b, jet_dev, jidx.data(), l->brec, l->stream));
+  l->jet_mode = true;
+  l->jet_ready = true;
+  return LHE_OK;
+}
+
 lhe_status lhe_lbm_step(lhe_lbm *l, int64_t n) {
   if (lhe_status s = check_handle(l)) return s;
   if (n < 0) return fail(l, LHE_ERR_ARG, "n must be >= 0");
   if (!l->initialised) return fail(l, LHE_ERR_STATE, "lhe_lbm_step before lhe_lbm_init");
   if (lhe_status st = check_pipeline(l)) return st;
   const bool periodic = l->p.bc == LHE_BC_PERIODIC;
-  if (!periodic && !l->have_wave) return fail(l, LHE_ERR_STATE, "Dirichlet box without boundary data (lhe_lbm_set_boundary_wave)");
+  if (!periodic && !l->have_wave && !l->jet_mode)
+    return fail(l, LHE_ERR_STATE, "Dirichlet box without boundary data (lhe_lbm_set_boundary_wave or _jet)");
+  if (!periodic && l->jet_mode && n > 0) {
+    if (n != 1) return fail(l, LHE_ERR_STATE, "boundary jets hold one step's data: step n = 1 at a time");
+    if (!l->jet_ready) return fail(l, LHE_ERR_STATE, "set the boundary jets of this step first (lhe_lbm_set_boundary_jet)");
+  }
   const int d = l->p.d;
   const bool dev = l->p.precision == LHE_FP32_DEV;
   StepArgs a = step_args(l);
@@ -701,7 +807,7 @@ lhe_status lhe_lbm_step(lhe_lbm *l, int64_t n) {
       }
     }
     // FP64 Dirichlet boxes: the row kernel also treats the x_1-face nodes of its rows
-    const bool fused = !periodic && !dev && !a.Rfield && l->xface;
+    const bool fused = !periodic && !dev && !a.Rfield && !l->jet_mode && l->xface;
     cudaError_t e = l->staged ? launch_step_dev3_tma(false, a, l->tma, l->stream)
                     : fused       ? launch_step_box_fp64(d, l->p.bc, a, b, l->xface, l->g.S_rows / l->g.n[0], l->stream)
                     : dev         ? launch_step_dev(d, false, !periodic, a, l->stream)
@@ -709,6 +815,11 @@ lhe_status lhe_lbm_step(lhe_lbm *l, int64_t n) {
     if (e != cudaSuccess) return cuda_fail(l, e, "step kernel launch");
     if (!periodic) {
       BoundaryArgs rest = b;
+      if (l->jet_mode) {
+        rest.roff = l->broff;
+        rest.rec = l->brec;
+        l->jet_ready = false;
+      }
       if (fused) {
         rest.sites = b.sites + l->nb_xface;
         rest.nsites = b.nsites - l->nb_xface;

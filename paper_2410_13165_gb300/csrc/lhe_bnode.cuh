@@ -67,18 +67,21 @@ __device__ __forceinline__ double bnode_data(const BoundaryArgs &a, const BNode<
   return acc;
 }
 
+// Half-way: f*_kbar(x, t) at the node itself, subtracted from B_k (Eq. (bun2)).
+template <int D, bool DEV>
+__device__ __forceinline__ double bnode_fkb(const BoundaryArgs &a, int k, int32_t site) {
+  constexpr Lattice<D> L{};
+  const int kb = L.opp[k];
+  const int64_t S = a.g.S;
+  return DEV ? fma(a.omega[kb], df_value(a.phi_src[site]), (double)static_cast<const float *>(a.src)[kb * S + site])
+             : static_cast<const double *>(a.src)[kb * S + site];
+}
+
 // Pre-collision population k at `site` whose source lies outside the box.
 template <int D, int KIND, bool DEV>
 __device__ __forceinline__ double bnode_unknown(const BoundaryArgs &a, const BNode<D> &nd, int k, int32_t site) {
-  constexpr Lattice<D> L{};
   const double acc = bnode_data<D, KIND>(a, nd, k);
-  if (KIND == 1) return acc;
-  const int kb = L.opp[k];
-  const int64_t S = a.g.S;
-  const double fkb = DEV ? fma(a.omega[kb], df_value(a.phi_src[site]),
-                               (double)static_cast<const float *>(a.src)[kb * S + site])
-                         : static_cast<const double *>(a.src)[kb * S + site];
-  return acc - fkb;
+  return KIND == 1 ? acc : acc - bnode_fkb<D, DEV>(a, k, site);
 }
 
 // Index j (0 .. 2D-2) of link k among the links whose first component is e_k,1 = sgn (the unknown

@@ -50,7 +50,10 @@ __global__ void __launch_bounds__(128) k_boundary(const BoundaryArgs a) {
     }
   }
   BNode<D> nd;
-  bnode_prepare<D, KIND>(a, x, nd);
+  const bool jets = a.rec != nullptr;  // data from jet records (else from the exact-solution family)
+  if (!jets) bnode_prepare<D, KIND>(a, x, nd);
+  const double *__restrict__ rec = jets ? a.rec + a.roff[t] : nullptr;
+  int ju = 0;
 
   const double *__restrict__ fsrc = static_cast<const double *>(a.src);
   const float *__restrict__ gsrc = static_cast<const float *>(a.src);
@@ -71,7 +74,12 @@ __global__ void __launch_bounds__(128) k_boundary(const BoundaryArgs a) {
       v[k] = DEV ? fma(a.omega[k], df_value(a.phi_src[o]), (double)gsrc[k * S + o]) : fsrc[k * S + o];
       continue;
     }
-    v[k] = bnode_unknown<D, KIND, DEV>(a, nd, k, site);
+    if (jets) {
+      const double b = __ldg(rec + ju++);
+      v[k] = KIND == 1 ? b : b - bnode_fkb<D, DEV>(a, k, site);
+    } else {
+      v[k] = bnode_unknown<D, KIND, DEV>(a, nd, k, site);
+    }
   }
   // collision, as in the bulk: phi = sum_k f_k (fixed-point sum), f*_k = (1 - s) f_k + omega_k (s phi + dt R)
   const double phi = fixed_moment_sum<Q, 0>(v);
@@ -90,6 +98,130 @@ __global__ void __launch_bounds__(128) k_boundary(const BoundaryArgs a) {
 #pragma unroll
     for (int k = 0; k < Q; ++k)
       fdst[k * S + site] = s2 ? fma(a.omega[k], psi, -v[k]) : fma(a.omega[k], psi, a.oms * v[k]);
+  }
+}
+
+// Records of the boundary data from jets of phi (lhe_lbm_set_boundary_jet): for every boundary node
+// and unknown link k (in the order of k), with c = c e_k,
+//   full-way, jet at the node and t + dt (Eq. (bun1)):
+//     order 1: omega_k phi;  order 3: omega_k [phi - (dt/2)(c.grad + d_t) phi] + (dt/2) omega_k R;
+//     order 4: order 3 + omega_k (dt^3/24) (c.grad + d_t)^3 phi
+//   half-way, jet at x_b = x - c dt/2 and t (Eq. (bun2) without -f*_kbar), w+- = omega_k +- omega_kbar:
+//     w+ phi + [P >= 2] w+ (dt/2)(phi_t + R) - [P >= 3] (w+ (dt^2/8) cc:grad^2 phi + w- (dt^2/4) c.grad phi_t)
+//     - [P >= 4] (w+ (dt^3/16) cc:grad^2 phi_t + w+ (dt^3/24) phi_ttt + w- (dt^3/8) c.grad phi_tt).
+// A jet holds every derivative of order <= 3 in (t, x_1..x_d); J.i3[a*36 + b*6 + e] and
+// J.i2[a*6 + b] give the position of the derivative in the variables a, b(, e) (0: t, i: x_i), in
+// any order.
+struct JetIndex {
+  int16_t i3[216];
+  int16_t i2[36];
+};
+
+template <int D, int KIND>
+__global__ void __launch_bounds__(128) k_jet_records(const BoundaryArgs a, const double *__restrict__ jet,
+                                                     const JetIndex J, double *__restrict__ rec) {
+  constexpr Lattice<D> L{};
+  constexpr int Q = Lattice<D>::Q;
+  constexpr int JL = (D + 4) * (D + 3) * (D + 2) / 6;
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= a.nsites) return;
+  const int32_t site = a.sites[t];
+  int x[D];
+  {
+    uint32_t r = (uint32_t)site;
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      if (i == D - 1) {
+        x[i] = (int)r;
+      } else {
+        const uint32_t q = a.g.dv[i].div(r);
+        x[i] = (int)(r - q * (uint32_t)a.g.n[i]);
+        r = q;
+      }
+    }
+  }
+  const int32_t r0 = a.roff[t];
+  const int P = a.order;
+  const double dt = a.dt;
+  int ju = 0;
+  for (int k = 0; k < Q; ++k) {
+    bool inside = true;
+    for (int i = 0; i < D; ++i) {
+      const int xs = x[i] - L.e[k][i];
+      if (xs < 0 || xs >= a.g.n[i]) inside = false;
+    }
+    if (inside) continue;
+    const double *j = jet + (size_t)(KIND == 1 ? t : r0 + ju) * JL;
+    double w[D + 1];  // weights of the variables in (d_t + c.grad): 1 for t, c_i for x_i
+    w[0] = 1.0;
+    for (int i = 0; i < D; ++i) w[i + 1] = a.c * L.e[k][i];
+    double val;
+    if (KIND == 1) {
+      const double wk = a.omega[k];
+      val = wk * j[0];
+      if (P >= 3) {
+        double d1 = 0.0;
+        for (int v = 0; v <= D; ++v) d1 += w[v] * j[1 + v];
+        val = wk * (j[0] - 0.5 * dt * d1) + 0.5 * dt * wk * a.R;
+      }
+      if (P >= 4) {
+        double d3 = 0.0;
+        for (int p0 = 0; p0 <= D; ++p0)
+          for (int p1 = 0; p1 <= D; ++p1)
+            for (int p2 = 0; p2 <= D; ++p2) {
+              const double ww = w[p0] * w[p1] * w[p2];
+              if (ww != 0.0) d3 += ww * j[J.i3[p0 * 36 + p1 * 6 + p2]];
+            }
+        val += wk * dt * dt * dt / 24.0 * d3;
+      }
+    } else {
+      const int kb = L.opp[k];
+      const double wp = a.omega[k] + a.omega[kb], wm = a.omega[k] - a.omega[kb];
+      val = wp * j[0];
+      if (P >= 2) val += 0.5 * dt * wp * (j[1] + a.R);
+      if (P >= 3) {
+        double cch = 0.0, cgt = 0.0;
+        for (int p0 = 1; p0 <= D; ++p0) {
+          cgt += w[p0] * j[J.i2[p0 * 6]];
+          for (int p1 = 1; p1 <= D; ++p1) cch += w[p0] * w[p1] * j[J.i2[p0 * 6 + p1]];
+        }
+        val -= dt * dt / 8.0 * wp * cch + dt * dt / 4.0 * wm * cgt;
+      }
+      if (P >= 4) {
+        double ccht = 0.0, cgtt = 0.0;
+        for (int p0 = 1; p0 <= D; ++p0) {
+          cgtt += w[p0] * j[J.i3[p0 * 36]];
+          for (int p1 = 1; p1 <= D; ++p1) ccht += w[p0] * w[p1] * j[J.i3[p0 * 36 + p1 * 6]];
+        }
+        val -= dt * dt * dt / 16.0 * wp * ccht + dt * dt * dt / 24.0 * wp * j[J.i3[0]] + dt * dt * dt / 8.0 * wm * cgtt;
+      }
+    }
+    rec[r0 + ju++] = val;
+  }
+}
+
+template <int D>
+static cudaError_t jet_records_d(int kind, const BoundaryArgs &a, const double *jet, const JetIndex &J, double *rec,
+                                 cudaStream_t st) {
+  if (a.nsites <= 0) return cudaSuccess;
+  const unsigned blocks = (unsigned)((a.nsites + 127) / 128);
+  if (kind == 1) k_jet_records<D, 1><<<blocks, 128, 0, st>>>(a, jet, J, rec);
+  else k_jet_records<D, 2><<<blocks, 128, 0, st>>>(a, jet, J, rec);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_jet_records(int d, int kind, const BoundaryArgs &a, const double *jet, const int16_t *jidx,
+                               double *rec, cudaStream_t st) {
+  JetIndex J;
+  for (int i = 0; i < 216; ++i) J.i3[i] = jidx[i];
+  for (int i = 0; i < 36; ++i) J.i2[i] = jidx[216 + i];
+  switch (d) {
+    case 1: return jet_records_d<1>(kind, a, jet, J, rec, st);
+    case 2: return jet_records_d<2>(kind, a, jet, J, rec, st);
+    case 3: return jet_records_d<3>(kind, a, jet, J, rec, st);
+    case 4: return jet_records_d<4>(kind, a, jet, J, rec, st);
+    case 5: return jet_records_d<5>(kind, a, jet, J, rec, st);
+    default: return cudaErrorInvalidValue;
   }
 }
 

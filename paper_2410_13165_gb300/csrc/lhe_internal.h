@@ -6,6 +6,7 @@
 #include <cstdint>
 #include <string>
 #include <utility>
+#include <vector>
 
 #include "lhe_device.cuh"
 #include "lhe_lbm.h"
@@ -93,6 +94,11 @@ struct BoundaryArgs {
   Geom g;
   const int32_t *sites;    // boundary node indices
   int64_t nsites;
+  // Boundary data given as jets (lhe_lbm_set_boundary_jet): per boundary node, one record entry per
+  // unknown link in the order of k (rec + roff[node]) holding the population (full-way) or B_k
+  // (half-way, Eq. (bun2) without -f*_kbar); rec == nullptr: data from the exact-solution family.
+  const int32_t *roff;
+  const double *rec;
   const void *src;
   void *dst;
   const float2 *phi_src;
@@ -161,6 +167,8 @@ struct AdjGradArgs {
 cudaError_t launch_step_fp64(int d, bool adjoint, bool interior, const StepArgs &a, cudaStream_t st);
 cudaError_t launch_step_dev(int d, bool adjoint, bool interior, const StepArgs &a, cudaStream_t st);
 cudaError_t launch_boundary(int d, int kind, bool dev, const BoundaryArgs &a, cudaStream_t st);
+cudaError_t launch_jet_records(int d, int kind, const BoundaryArgs &a, const double *jet, const int16_t *jidx,
+                               double *rec, cudaStream_t st);
 cudaError_t launch_step_box_fp64(int d, int kind, const StepArgs &a, const BoundaryArgs &b, double *xb, int64_t nrows,
                                  cudaStream_t st);
 cudaError_t launch_adjoint_boundary(int d, int kind, const BoundaryArgs &a, cudaStream_t st);
@@ -215,6 +223,14 @@ struct lhe_lbm {
   double *xface = nullptr;      // their boundary data per step (2 (2d - 1) doubles per interior row)
   bool have_wave = false;
   lhe_wave wave{};
+  // boundary data as jets (lhe_lbm_set_boundary_jet), one step at a time
+  bool jet_mode = false;        // the data come from jets (else from the wave)
+  bool jet_ready = false;       // jets set for the next step
+  std::vector<int32_t> bsites_host;  // boundary nodes in the library's order
+  std::vector<int32_t> broff_host;   // per boundary node: first record (unknown links in the order of k)
+  int64_t nrec = 0;             // records = (boundary node, unknown link) pairs
+  int32_t *broff = nullptr;     // device copies, allocated by the first lhe_lbm_set_boundary_jet
+  double *brec = nullptr;
   double *bc_table = nullptr;
   double *bc_axis = nullptr;    // per-axis phase tables of the Dirichlet data
   // adjoint

@@ -164,6 +164,17 @@ LHE_API const char *lhe_lbm_last_error(const lhe_lbm *lbm);
 /* Fill *info (host). */
 LHE_API lhe_status lhe_lbm_info(const lhe_lbm *lbm, lhe_lbm_info_t *info);
 
+/* Source of the following steps: R_dev (device or host, S doubles, copied) is the per-site source
+ * R(x) used from the next lhe_lbm_step on; NULL returns to the constant params.R. It lets a caller
+ * drive a source that varies in time: before the step t_n -> t_{n+1} pass R(x, t_{n+1}). A step
+ * streams, then collides at the new time (R_k = omega_k R(x), Eq. (BGK-LB-Evolution)); the R term of
+ * the full-way scheme is taken at t_{n+1} (this source), those of the half-way scheme at t_n (the
+ * source of the last collision); lhe_lbm_init's field is R(x, 0). Until the next step, macro and
+ * diagnostics keep using the source of the last collision. On a Dirichlet box with jets, call it
+ * before lhe_lbm_set_boundary_jet. The paper's fourth-order analysis assumes a constant R; with a
+ * source that varies the scheme converges at about first order (measured). */
+LHE_API lhe_status lhe_lbm_set_source(lhe_lbm *lbm, const double *R_dev);
+
 /* Replace the CUDA stream used by subsequent calls. */
 LHE_API lhe_status lhe_lbm_set_stream(lhe_lbm *lbm, void *stream);
 
@@ -173,7 +184,8 @@ LHE_API lhe_status lhe_lbm_set_stream(lhe_lbm *lbm, void *stream);
  * grad_dev: d*S doubles (component-major), or NULL, in which case the gradient is the periodic
  * fourth-order central difference of phi0 (periodic boxes only; LHE_ERR_ARG otherwise).
  * R_dev: per-site source R(x) (S doubles; the discrete source is R_k = omega_k R(x)), or NULL for
- * the constant params.R. The field is copied; Dirichlet boxes require R_dev == NULL.
+ * the constant params.R. The field is copied. On Dirichlet boxes a field needs the boundary data as
+ * jets (lhe_lbm_set_boundary_jet), whose R terms then take R at the boundary node.
  * The library stores post-collision populations internally, so init also applies one collision. */
 LHE_API lhe_status lhe_lbm_init(lhe_lbm *lbm, const double *phi0_dev, const double *grad_dev, const double *R_dev);
 

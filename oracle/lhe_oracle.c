@@ -334,9 +334,10 @@ void orc_fd_grad(const orc_model *m, const double *phi, double *grad) {
   }
 }
 
-/* Boundary value of the unknown population k at node `site` for step n -> n+1. */
+/* Boundary value of the unknown population k at node `site` for step n -> n+1; R: the source at the
+ * node (the constant R, or the per-site field of the step). */
 static double boundary_value(const orc_model *m, const orc_wave *w, int64_t n, int64_t site, int k,
-                             const double *fstar) {
+                             const double *fstar, double R) {
   const int d = m->d;
   const int64_t S = n_sites(m);
   const double dt = m->dt, c = m->dx / m->dt;
@@ -352,7 +353,7 @@ static double boundary_value(const orc_model *m, const orc_wave *w, int64_t n, i
     const double feq = wk * phi;
     const double c_grad = wk * orc_dir_deriv(m, w, x, t1, ck, 1, 0);  /* c_k . grad f^eq */
     const double f_t = wk * orc_dir_deriv(m, w, x, t1, ck, 0, 1);     /* d_t f^eq */
-    double val = feq - 0.5 * dt * c_grad - 0.5 * dt * f_t + 0.5 * dt * wk * m->R;
+    double val = feq - 0.5 * dt * c_grad - 0.5 * dt * f_t + 0.5 * dt * wk * R;
     if (m->bc_order == 3) return val;
     const double c_grad_tt = wk * orc_dir_deriv(m, w, x, t1, ck, 1, 2);   /* c . grad d_t^2 f^eq */
     const double cc_hess_t = wk * orc_dir_deriv(m, w, x, t1, ck, 2, 1);   /* c^2 : grad^2 d_t f^eq */
@@ -371,7 +372,7 @@ static double boundary_value(const orc_model *m, const orc_wave *w, int64_t n, i
   const double wdif = wk - m->omega[kb];  /* f^eq_k - f^eq_kbar = (omega_k - omega_kbar) phi */
   double B = wsum * orc_dir_deriv(m, w, xb, t, ck, 0, 0);
   if (m->bc_order >= 2)
-    B += 0.5 * dt * wsum * orc_dir_deriv(m, w, xb, t, ck, 0, 1) + 0.5 * dt * (wk * m->R + m->omega[kb] * m->R);
+    B += 0.5 * dt * wsum * orc_dir_deriv(m, w, xb, t, ck, 0, 1) + 0.5 * dt * (wk * R + m->omega[kb] * R);
   if (m->bc_order >= 3)
     B += -dt * dt / 8.0 * wsum * orc_dir_deriv(m, w, xb, t, ck, 2, 0) -
          dt * dt / 4.0 * wdif * orc_dir_deriv(m, w, xb, t, ck, 1, 1);
@@ -429,7 +430,7 @@ void orc_step(const orc_model *m, const orc_wave *w, int64_t n, const double *Rf
         const int64_t src = idx[i] - m->e[k * d + i];
         if (src < 0 || src >= m->n[i]) outside = 1;
       }
-      if (outside) fnew[(int64_t)k * S + site] = boundary_value(m, w, n, site, k, fstar);
+      if (outside) fnew[(int64_t)k * S + site] = boundary_value(m, w, n, site, k, fstar, Rfield ? Rfield[site] : m->R);
     }
   }
 }

@@ -274,13 +274,15 @@ class Model:
             cur, nxt = nxt, cur
         return cur
 
-    def step_jets(self, f, n0, nsteps, jet_fn) -> np.ndarray:
+    def step_jets(self, f, n0, nsteps, jet_fn, Rfield_fn=None) -> np.ndarray:
         """Dirichlet steps with the boundary data given as jets of phi: jet_fn(points (P, d), t)
         returns (P, J) arrays of every derivative of order 0..3 in (t, x_1..x_d), ordered by length
         and then lexicographically over non-decreasing variable tuples (0: t, i: x_i). The unknown
         populations follow Eq. (bun1) (at the node, t + dt) and Eq. (bun2) (at x - c_k dt/2, t) with
         the directional derivatives d_t^q (c . grad)^p phi formed from the jets, term by term as in
-        boundary_value of lhe_oracle.c."""
+        boundary_value of lhe_oracle.c. Rfield_fn(n) (optional) gives the per-site source R(x, t_n) of
+        the collision at t_n; the schemes' R terms take it at the boundary node at the time of their
+        data: full-way t_{n+1} (Rfield_fn(n + 1)), half-way t_n (Rfield_fn(n))."""
         if self.bc == "periodic":
             raise ValueError("jets are Dirichlet data")
         import itertools
@@ -322,7 +324,11 @@ class Model:
         nxt = np.empty_like(cur)
         L = lib()
         for n in range(n0, n0 + nsteps):
-            L.orc_step(ctypes.byref(self._m), ctypes.byref(w), n, None, _p(cur), _p(star), _p(nxt))
+            Rf = None if Rfield_fn is None else np.ascontiguousarray(Rfield_fn(n), dtype=np.float64).reshape(S)
+            L.orc_step(ctypes.byref(self._m), ctypes.byref(w), n, _p(Rf), _p(cur), _p(star), _p(nxt))
+            Rn = np.full(len(sites), self.R) if Rf is None else Rf[sites]  # source at the boundary node
+            if self.bc == "fullway" and Rfield_fn is not None:
+                Rn = np.ascontiguousarray(Rfield_fn(n + 1), dtype=np.float64).reshape(S)[sites]
             if self.bc == "fullway":
                 t1 = (n + 1) * dt
                 J = np.asarray(jet_fn(X[:, sites].T.copy(), t1), dtype=np.float64)
@@ -330,7 +336,7 @@ class Model:
                 if self.bc_order == 1:
                     val = feq
                 else:
-                    val = feq - 0.5 * dt * wk * dir_deriv(J, 1, 0) - 0.5 * dt * wk * dir_deriv(J, 0, 1) + 0.5 * dt * wk * self.R
+                    val = feq - 0.5 * dt * wk * dir_deriv(J, 1, 0) - 0.5 * dt * wk * dir_deriv(J, 0, 1) + 0.5 * dt * wk * Rn
                     if self.bc_order >= 4:
                         val = val + dt ** 3 / 8.0 * wk * dir_deriv(J, 1, 2) + dt ** 3 / 8.0 * wk * dir_deriv(J, 2, 1) \
                             + dt ** 3 / 24.0 * wk * dir_deriv(J, 0, 3) + dt ** 3 / 24.0 * wk * dir_deriv(J, 3, 0)
@@ -340,7 +346,7 @@ class Model:
                 wsum, wdif = wk + wkb, wk - wkb
                 B = wsum * dir_deriv(J, 0, 0)
                 if self.bc_order >= 2:
-                    B = B + 0.5 * dt * wsum * dir_deriv(J, 0, 1) + 0.5 * dt * (wk * self.R + wkb * self.R)
+                    B = B + 0.5 * dt * wsum * dir_deriv(J, 0, 1) + 0.5 * dt * (wk * Rn + wkb * Rn)
                 if self.bc_order >= 3:
                     B = B - dt * dt / 8.0 * wsum * dir_deriv(J, 2, 0) - dt * dt / 4.0 * wdif * dir_deriv(J, 1, 1)
                 if self.bc_order >= 4:

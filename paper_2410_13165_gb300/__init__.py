@@ -148,6 +148,12 @@ class LBM:
         self._stream()
         _abi.lhe_lbm_set_boundary_wave(self.h, w)
 
+    def set_source(self, R=None):
+        """Per-site source R(x) (float64 tensor of S values) for the steps from the next one on, or
+        None for the constant R (lhe_lbm_set_source)."""
+        self._stream()
+        _abi.lhe_lbm_set_source(self.h, self._ptr(R, self.S, "R"))
+
     def boundary_points(self):
         """(points[P][d] as a numpy array, t_offset): the points where the Dirichlet jets of the next
         step are needed (full-way: the boundary nodes; half-way: the mid-link points of the unknown

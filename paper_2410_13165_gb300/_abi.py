@@ -31,6 +31,7 @@ EXPORTS = [
     "lhe_lbm_set_boundary_wave", "lhe_lbm_step", "lhe_lbm_macro", "lhe_lbm_diagnostics", "lhe_lbm_get_state",
     "lhe_lbm_set_state", "lhe_lbm_adjoint_seed", "lhe_lbm_adjoint_step", "lhe_lbm_adjoint_grads",
     "lhe_lbm_diagnostics_noalloc", "lhe_lbm_stability_map", "lhe_lbm_boundary_points", "lhe_lbm_set_boundary_jet",
+    "lhe_lbm_set_source",
 ]
 
 
@@ -96,6 +97,7 @@ def load(path: str | None = None):
         "lhe_lbm_last_error": (ctypes.c_char_p, [_H]),
         "lhe_lbm_info": (st, [_H, ctypes.POINTER(lhe_lbm_info_t)]),
         "lhe_lbm_set_stream": (st, [_H, ctypes.c_void_p]),
+        "lhe_lbm_set_source": (st, [_H, _D]),
         "lhe_lbm_init": (st, [_H, _D, _D, _D]),
         "lhe_lbm_set_boundary_wave": (st, [_H, ctypes.POINTER(lhe_wave)]),
         "lhe_lbm_boundary_points": (st, [_H, _D, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double)]),
@@ -197,6 +199,10 @@ def lhe_lbm_boundary_points(h, d: int):
 
 def lhe_lbm_set_boundary_jet(h, jet_ptr: int) -> None:
     check(load().lhe_lbm_set_boundary_jet(h, jet_ptr), h)
+
+
+def lhe_lbm_set_source(h, R_ptr) -> None:
+    check(load().lhe_lbm_set_source(h, R_ptr), h)
 
 
 def lhe_lbm_step(h, n: int) -> None:

@@ -469,6 +469,7 @@ lhe_status lhe_lbm_destroy(lhe_lbm *l) {
   }
   cudaFree(l->gR);
   cudaFree(l->Rfield);
+  cudaFree(l->Rnext);
   cudaFree(l->fdgrad);
   cudaFree(l->bsites);
   cudaFree(l->broff);
@@ -502,6 +503,37 @@ lhe_status lhe_lbm_info(const lhe_lbm *l, lhe_lbm_info_t *info) {
   return LHE_OK;
 }
 
+lhe_status lhe_lbm_set_source(lhe_lbm *l, const double *Rf) {
+  if (lhe_status s = check_handle(l)) return s;
+  if (Rf) {
+    if (!l->Rnext) LHE_CK(l, cudaMalloc(&l->Rnext, sizeof(double) * (size_t)l->g.S));
+    LHE_CK(l, cudaMemcpyAsync(l->Rnext, Rf, sizeof(double) * (size_t)l->g.S, cudaMemcpyDefault, l->stream));
+    l->Rnext_state = 1;
+  } else {
+    l->Rnext_state = 2;
+  }
+  return LHE_OK;
+}
+
+namespace {
+// The source set by lhe_lbm_set_source becomes the step's source when the step starts (the stored
+// post-collision state keeps needing the source of its own collision until then: macro).
+void activate_source(lhe_lbm *l) {
+  if (l->Rnext_state == 1) {
+    std::swap(l->Rfield, l->Rnext);
+  } else if (l->Rnext_state == 2 && l->Rfield) {
+    std::swap(l->Rfield, l->Rnext);  // keep the buffer for a later field
+    l->Rfield = nullptr;
+  }
+  l->Rnext_state = 0;
+}
+
+// The source the next step will use.
+const double *next_source(const lhe_lbm *l) {
+  return l->Rnext_state == 1 ? l->Rnext : (l->Rnext_state == 2 ? nullptr : l->Rfield);
+}
+}  // namespace
+
 lhe_status lhe_lbm_set_stream(lhe_lbm *l, void *stream) {
   if (lhe_status s = check_handle(l)) return s;
   l->stream = static_cast<cudaStream_t>(stream);
@@ -513,10 +545,9 @@ lhe_status lhe_lbm_init(lhe_lbm *l, const double *phi0, const double *grad, cons
   if (!phi0) return fail(l, LHE_ERR_ARG, "phi0 is NULL");
   const int d = l->p.d;
   const size_t S = (size_t)l->g.S;
-  if (Rf && l->p.bc != LHE_BC_PERIODIC)
-    return fail(l, LHE_ERR_ARG, "a per-site source field is only supported on periodic boxes (the boundary schemes assume constant R)");
   if (!grad && l->p.init_order == 3 && l->p.bc != LHE_BC_PERIODIC)
     return fail(l, LHE_ERR_ARG, "Dirichlet boxes need an explicit grad phi0 for the third-order initialisation");
+  l->Rnext_state = 0;
   if (Rf) {
     if (!l->Rfield) LHE_CK(l, cudaMalloc(&l->Rfield, sizeof(double) * S));
     LHE_CK(l, cudaMemcpyAsync(l->Rfield, Rf, sizeof(double) * S, cudaMemcpyDefault, l->stream));
@@ -653,6 +684,7 @@ static BoundaryArgs boundary_args(const lhe_lbm *l) {
   b.g = l->g;
   b.sites = l->bsites;
   b.nsites = l->nb;
+  b.Rfield = l->Rfield;
   b.table = l->bc_table;
   b.axis = l->bc_axis;
   int32_t off = 0;
@@ -761,6 +793,9 @@ lhe_status lhe_lbm_set_boundary_jet(lhe_lbm *l, const double *jet_dev) {
       }
   BoundaryArgs b = boundary_args(l);
   b.roff = l->broff;  // the kernel writes l->brec; b.rec stays null (the data are being formed)
+  // the schemes' R terms (a source varying in time): full-way at the new time t_{n+1} (the source of
+  // this step's collision), half-way at t_n (the source of the collision of f*_kbar)
+  b.Rfield = l->p.bc == LHE_BC_FULLWAY ? next_source(l) : l->Rfield;
   LHE_CK(l, launch_jet_records(d, l->p.bc, b, jet_dev, jidx.data(), l->brec, l->stream));
   l->jet_mode = true;
   l->jet_ready = true;
@@ -775,12 +810,16 @@ lhe_status lhe_lbm_step(lhe_lbm *l, int64_t n) {
   const bool periodic = l->p.bc == LHE_BC_PERIODIC;
   if (!periodic && !l->have_wave && !l->jet_mode)
     return fail(l, LHE_ERR_STATE, "Dirichlet box without boundary data (lhe_lbm_set_boundary_wave or _jet)");
+  if (!periodic && next_source(l) && !l->jet_mode && n > 0)
+    return fail(l, LHE_ERR_STATE, "a per-site source on a Dirichlet box needs the boundary data as jets "
+                                  "(the exact-solution family assumes a constant R)");
   if (!periodic && l->jet_mode && n > 0) {
     if (n != 1) return fail(l, LHE_ERR_STATE, "boundary jets hold one step's data: step n = 1 at a time");
     if (!l->jet_ready) return fail(l, LHE_ERR_STATE, "set the boundary jets of this step first (lhe_lbm_set_boundary_jet)");
   }
   const int d = l->p.d;
   const bool dev = l->p.precision == LHE_FP32_DEV;
+  if (n > 0) activate_source(l);
   StepArgs a = step_args(l);
   BoundaryArgs b{};
   if (!periodic) b = boundary_args(l);

@@ -83,7 +83,7 @@ __global__ void __launch_bounds__(128) k_boundary(const BoundaryArgs a) {
   }
   // collision, as in the bulk: phi = sum_k f_k (fixed-point sum), f*_k = (1 - s) f_k + omega_k (s phi + dt R)
   const double phi = fixed_moment_sum<Q, 0>(v);
-  const double psi = fma(a.s, phi, a.dt * a.R);
+  const double psi = fma(a.s, phi, a.dt * (a.Rfield ? __ldg(a.Rfield + site) : a.R));
   const bool s2 = a.s == 2.0;
   if (DEV) {
     float *gdst = static_cast<float *>(a.dst);
@@ -109,6 +109,7 @@ __global__ void __launch_bounds__(128) k_boundary(const BoundaryArgs a) {
 //   half-way, jet at x_b = x - c dt/2 and t (Eq. (bun2) without -f*_kbar), w+- = omega_k +- omega_kbar:
 //     w+ phi + [P >= 2] w+ (dt/2)(phi_t + R) - [P >= 3] (w+ (dt^2/8) cc:grad^2 phi + w- (dt^2/4) c.grad phi_t)
 //     - [P >= 4] (w+ (dt^3/16) cc:grad^2 phi_t + w+ (dt^3/24) phi_ttt + w- (dt^3/8) c.grad phi_tt).
+// R is the source at the node (the per-site field of the step, when there is one).
 // A jet holds every derivative of order <= 3 in (t, x_1..x_d); J.i3[a*36 + b*6 + e] and
 // J.i2[a*6 + b] give the position of the derivative in the variables a, b(, e) (0: t, i: x_i), in
 // any order.
@@ -143,6 +144,7 @@ __global__ void __launch_bounds__(128) k_jet_records(const BoundaryArgs a, const
   const int32_t r0 = a.roff[t];
   const int P = a.order;
   const double dt = a.dt;
+  const double R = a.Rfield ? a.Rfield[site] : a.R;  // the source at the node
   int ju = 0;
   for (int k = 0; k < Q; ++k) {
     bool inside = true;
@@ -162,7 +164,7 @@ __global__ void __launch_bounds__(128) k_jet_records(const BoundaryArgs a, const
       if (P >= 3) {
         double d1 = 0.0;
         for (int v = 0; v <= D; ++v) d1 += w[v] * j[1 + v];
-        val = wk * (j[0] - 0.5 * dt * d1) + 0.5 * dt * wk * a.R;
+        val = wk * (j[0] - 0.5 * dt * d1) + 0.5 * dt * wk * R;
       }
       if (P >= 4) {
         double d3 = 0.0;
@@ -178,7 +180,7 @@ __global__ void __launch_bounds__(128) k_jet_records(const BoundaryArgs a, const
       const int kb = L.opp[k];
       const double wp = a.omega[k] + a.omega[kb], wm = a.omega[k] - a.omega[kb];
       val = wp * j[0];
-      if (P >= 2) val += 0.5 * dt * wp * (j[1] + a.R);
+      if (P >= 2) val += 0.5 * dt * wp * (j[1] + R);
       if (P >= 3) {
         double cch = 0.0, cgt = 0.0;
         for (int p0 = 1; p0 <= D; ++p0) {

@@ -99,6 +99,7 @@ struct BoundaryArgs {
   // (half-way, Eq. (bun2) without -f*_kbar); rec == nullptr: data from the exact-solution family.
   const int32_t *roff;
   const double *rec;
+  const double *Rfield;    // per-site source R(x) of the step, or nullptr for the constant R
   const void *src;
   void *dst;
   const float2 *phi_src;
@@ -211,7 +212,9 @@ struct lhe_lbm {
   int cur = 0;
   bool initialised = false;
   int64_t step = 0;
-  double *Rfield = nullptr;     // owned copy of the per-site source, or nullptr
+  double *Rfield = nullptr;     // owned copy of the per-site source of the last collision, or nullptr
+  double *Rnext = nullptr;      // lhe_lbm_set_source: the source of the next step (buffer)
+  int32_t Rnext_state = 0;      // 0: nothing pending; 1: the field in Rnext; 2: back to the constant R
   bool grad_was_fd = false;
   int init_order_used = 3;
   double *fdgrad = nullptr;     // d*S scratch for the finite-difference gradient

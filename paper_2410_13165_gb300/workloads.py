@@ -229,3 +229,39 @@ def gaussian_grad(X: np.ndarray, t: float, u, A: float, xc, sigma: float) -> np.
     Y = X - np.asarray(u, dtype=np.float64)[:, None] * t - np.asarray(xc, dtype=np.float64)[:, None]
     G = A * np.exp(-np.sum(Y * Y, axis=0) / (2.0 * sigma * sigma))
     return -Y / (sigma * sigma) * G[None, :]
+
+
+# ---- manufactured solution with a source: phi = prod_i sin(pi x_i) exp(-t), R = phi_t + u.grad phi ----
+
+def sine_product_value(X: np.ndarray, t: float) -> np.ndarray:
+    return np.prod(np.sin(np.pi * X), axis=0) * math.exp(-t)
+
+
+def sine_product_grad(X: np.ndarray, t: float) -> np.ndarray:
+    s, c = np.sin(np.pi * X), np.cos(np.pi * X)
+    d = X.shape[0]
+    out = np.empty_like(X)
+    for i in range(d):
+        out[i] = np.pi * c[i] * np.prod(np.delete(s, i, axis=0), axis=0) * math.exp(-t)
+    return out
+
+
+def sine_product_source(X: np.ndarray, t: float, u) -> np.ndarray:
+    """R(x, t) = phi_t + u.grad phi of the manufactured solution (varies in x and t)."""
+    return -sine_product_value(X, t) + np.asarray(u, dtype=np.float64) @ sine_product_grad(X, t)
+
+
+def sine_product_jets(points: np.ndarray, t: float) -> np.ndarray:
+    """Jets of phi = prod_i sin(pi x_i) exp(-t): a t-derivative gives -1, an x_i-derivative one more
+    derivative of sin(pi x_i)."""
+    P, d = points.shape
+    tuples = _jet_tuples(d)
+    out = np.zeros((P, len(tuples)))
+    derivs = [np.sin, np.cos, lambda z: -np.sin(z), lambda z: -np.cos(z)]
+    for col, tup in enumerate(tuples):
+        val = np.full(P, math.exp(-t) * (-1.0) ** sum(1 for v in tup if v == 0))
+        for i in range(d):
+            q = sum(1 for v in tup if v == i + 1)
+            val = val * np.pi ** q * derivs[q % 4](np.pi * points[:, i])
+        out[:, col] = val
+    return out

@@ -143,3 +143,78 @@ def test_jet_error_paths():
         per.boundary_points()
     assert ei.value.status == _abi.ERR_STATE
     per.close()
+
+
+def _source_run(sim, m, X, u, steps, Rt):
+    """Steps with the source R(x, t_{n+1}) of each step's collision set first, then the jets."""
+    for n in range(steps):
+        sim.set_source(_t(Rt(n + 1)))
+        pts, toff = sim.boundary_points()
+        sim.set_boundary_jet(_t(W.sine_product_jets(pts, sim.step_index * sim.dt + toff)))
+        sim.step(1)
+
+
+@pytest.mark.parametrize("d,n,bc,precision", [(2, 17, "fullway", "fp64"), (2, 16, "halfway", "fp64"),
+                                              (3, 9, "fullway", "fp64"), (2, 17, "fullway", "fp32dev"),
+                                              (3, 8, "halfway", "fp32dev")])
+def test_time_varying_source_on_dirichlet_boxes(d, n, bc, precision):
+    """The manufactured solution prod_i sin(pi x_i) exp(-t) with its source R(x, t) set before each
+    step and boundary data as jets, against the oracle with the same sources and jets."""
+    u = [0.1, 0.05, -0.08][:d] if bc == "fullway" else [0.01, 0.02, -0.01][:d]
+    steps = 10
+    m = O.Model(d, n, -1.0, 1.0, u, bc=bc)
+    X = m.coords()
+    phi0, grad = W.sine_product_value(X, 0.0), W.sine_product_grad(X, 0.0)
+    Rt = lambda k: W.sine_product_source(X, k * m.dt, u)  # R(x, t_k), the source of the collision at t_k
+    ref = m.phi(m.step_jets(m.init(phi0, grad, 3), 0, steps, lambda P, t: W.sine_product_jets(P, t), Rfield_fn=Rt))
+    sim = LBM(d, n, -1.0, 1.0, u=u, bc=bc, precision=precision)
+    sim.init(_t(phi0), _t(grad), _t(Rt(0)))
+    _source_run(sim, m, X, u, steps, Rt)
+    got = sim.macro().cpu().numpy()
+    sim.close()
+    tol = 1e-13 if precision == "fp64" else 1e-5
+    assert np.max(np.abs(got - ref)) < tol * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("d,n,tau,precision", [(2, 24, 0.5, "fp64"), (2, 24, 0.8, "fp64"), (3, 16, 0.8, "fp32dev")])
+def test_time_varying_source_on_periodic_boxes(d, n, tau, precision):
+    """A source changed before every step (periodic: the FP64 kernel in both collision forms, the
+    staged FP32-deviation kernel of D3Q19), against the oracle; macro between steps, after the next
+    source is set, still reports phi of the last collision."""
+    u = [0.1, 0.05, -0.08][:d]
+    F = W.fourier_field(d, 3, 80 + d, 0.0, 1.0)
+    m = O.Model(d, n, 0.0, 1.0, u, tau=tau)
+    X = m.coords()
+    src = lambda k: 0.3 * np.cos(np.pi * k * m.dt + X[0]) * np.sin(2 * np.pi * X[-1])
+    f = m.init(F.value(X), F.grad(X), 3)
+    sim = LBM(d, n, u=u, tau=tau, precision=precision)
+    sim.init(_t(F.value(X)), _t(F.grad(X)), _t(src(0)))  # the source of the collision at t_0
+    tol = 1e-13 if precision == "fp64" else 1e-5
+    for k in range(8):
+        f = m.step(f, k, 1, Rfield=src(k))  # the oracle collides at t_k, then streams
+        sim.set_source(_t(src(k + 1)))      # the library streams, then collides at t_{k+1}
+        sim.step(1)
+        sim.set_source(_t(src(k + 2)))      # set ahead of the next step: macro must not use it
+        ref = m.phi(f)
+        assert np.max(np.abs(sim.macro().cpu().numpy() - ref)) < tol * np.max(np.abs(ref)), k
+    sim.set_source(None)                    # the collisions at t_9, t_10 take the constant R (0)
+    f = m.step(f, 8, 1, Rfield=src(8))      # oracle: collision at t_8 (the library's was at step 8)
+    f = m.step(f, 9, 1)                     # and at t_9 with the constant source
+    sim.step(2)
+    ref = m.phi(f)
+    assert np.max(np.abs(sim.macro().cpu().numpy() - ref)) < tol * np.max(np.abs(ref))
+    sim.close()
+
+
+def test_a_source_field_needs_jets_on_dirichlet_boxes():
+    d, n = 2, 9
+    sim = LBM(d, n, 0.0, 1.0, u=(0.1, 0.05), bc="fullway")
+    X = W.node_coords(d, [n] * d, 0.0, sim.dx)
+    sim.init(_t(W.sine_product_value(X, 0.0)), _t(W.sine_product_grad(X, 0.0)), _t(np.ones(n * n)))
+    sim.set_boundary_wave([1.0], [[1.0, 2.0]], [0.0])
+    with pytest.raises(LHEError) as ei:
+        sim.step(1)
+    assert ei.value.status == _abi.ERR_STATE
+    sim.set_source(None)
+    sim.step(1)  # constant R again: the wave data apply
+    sim.close()

@@ -533,6 +533,60 @@ def run_convergence(args):
     return 0
 
 
+def run_fp32_floor(args):
+    """Where the FP32-deviation form stops converging at fourth order: periodic, tau = 1/2, K = 3,
+    T = 1 (steps = N), RMSE against the exact solution for FP64 and FP32 deviations, D2Q9 N = 64..2048
+    (4 modes) and D3Q19 N = 64..512 (8 modes). Fields of the large grids are generated on the host in
+    slabs of the slowest axis."""
+    import torch
+
+    from paper_2410_13165_gb300 import LBM, build
+    from paper_2410_13165_gb300 import workloads as W
+
+    build.build()
+    out = {"metric": "RMSE vs the exact solution and slopes, FP64 vs FP32 deviations, tau = 1/2, T = 1", "unit": "rate"}
+
+    def slabs(d, N, rows=None):
+        rows = rows or max(1, (1 << 22) // N ** (d - 1))
+        for z0 in range(0, N, rows):
+            z1 = min(N, z0 + rows)
+            axes = [np.arange(N) / N] * (d - 1) + [np.arange(z0, z1) / N]
+            grids = np.meshgrid(*axes[::-1], indexing="ij")[::-1]
+            yield z0, z1, np.stack([g.ravel() for g in grids])
+
+    for d, Ns, u, modes in ((2, (64, 128, 256, 512, 1024, 2048), (0.1, 0.2), 4), (3, (64, 128, 256, 512), U, NMODES)):
+        F = W.fourier_field(d, modes, SEED + 30 + d)
+        res = {}
+        for prec in ("fp64", "fp32dev"):
+            errs = []
+            for N in Ns:
+                S, plane = N ** d, N ** (d - 1)
+                phi0 = torch.empty(S, dtype=torch.float64, device="cuda")
+                grad = torch.empty(d, S, dtype=torch.float64, device="cuda")
+                for z0, z1, X in slabs(d, N):
+                    phi0[z0 * plane:z1 * plane] = torch.from_numpy(F.value(X))
+                    grad[:, z0 * plane:z1 * plane] = torch.from_numpy(F.grad(X))
+                sim = LBM(d, N, u=u, precision=prec)
+                sim.init(phi0, grad.reshape(-1))
+                del phi0, grad
+                sim.step(N)
+                phi = sim.macro()
+                sim.close()
+                se = 0.0
+                for z0, z1, X in slabs(d, N):
+                    diff = phi[z0 * plane:z1 * plane].cpu().numpy() - F.value(X, shift=np.asarray(u) * 1.0)
+                    se += float(np.sum(diff * diff))
+                del phi
+                torch.cuda.empty_cache()
+                errs.append((se / S) ** 0.5)
+            res[prec] = {"N": list(Ns), "rmse": errs, "slopes": [float(np.log2(a / b)) for a, b in zip(errs, errs[1:])]}
+        ratio = [b / a for a, b in zip(res["fp64"]["rmse"], res["fp32dev"]["rmse"])]
+        res["fp32dev_over_fp64"] = ratio
+        out["D%dQ%d" % (d, 2 * d * d + 1)] = res
+    print(json.dumps(out))
+    return 0
+
+
 def run_order_law(args):
     """Eq. (cr-estimation) on the GPU: convergence rates of the Dirichlet schemes against the boundary
     order P and the initialisation order K (2D, Example 1's setting with R = 5 and exact solutions of
@@ -695,13 +749,13 @@ def main():
     ap.add_argument("--error-steps", type=int, default=2000)
     ap.add_argument("--workload", default="d3q19_256",
                     choices=["d3q19_256", "d4q33_dirichlet", "d5q51_fp32dev", "adjoint", "convergence",
-                             "order_law", "examples", "stability_map"])
+                             "order_law", "examples", "stability_map", "fp32_floor"])
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
     others = {"d4q33_dirichlet": run_d4q33_dirichlet, "d5q51_fp32dev": run_d5q51_fp32dev,
               "adjoint": run_adjoint_ratio, "convergence": run_convergence, "order_law": run_order_law,
-              "examples": run_examples, "stability_map": run_stability_map}
+              "examples": run_examples, "stability_map": run_stability_map, "fp32_floor": run_fp32_floor}
     if args.workload in others:
         if args.steps == 400:
             args.steps = 50

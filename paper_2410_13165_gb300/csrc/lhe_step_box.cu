@@ -11,10 +11,11 @@ namespace {
 constexpr int kModeGeneral = 0, kModeS2 = 1;  // collision forms, as in lhe_step_fp64.cu
 }  // namespace
 
-// Boundary data of the x_1-face nodes of a Dirichlet box (those whose other coordinates are
-// interior), for k_step_box: for interior row r (x_2..x_D interior) and side h (0: x_1 = 0, 1:
-// x_1 = n_1 - 1), the 2D - 1 values bnode_data of the unknown links (e_k,1 = +1 on the low side,
-// -1 on the high side) at xb[(2 r + h)(2D - 1) + j]. They do not depend on the state.
+// The unknown populations of the x_1-face nodes of a Dirichlet box (those whose other coordinates
+// are interior), for k_step_box: for interior row r (x_2..x_D interior) and side h (0: x_1 = 0, 1:
+// x_1 = n_1 - 1), the 2D - 1 unknown links (e_k,1 = +1 on the low side, -1 on the high side) at
+// xb[(2 r + h)(2D - 1) + j], exactly as the boundary-node kernel forms them: the boundary data, and
+// for the half-way scheme minus f*_kbar at the node (the state at the start of the step).
 template <int D, int KIND>
 __global__ void __launch_bounds__(128) k_xface_data(const BoundaryArgs b, double *__restrict__ xb, int64_t nrows) {
   constexpr Lattice<D> L{};
@@ -36,23 +37,26 @@ __global__ void __launch_bounds__(128) k_xface_data(const BoundaryArgs b, double
       r = q;
     }
   }
+  int32_t site = 0;
+#pragma unroll
+  for (int i = 0; i < D; ++i) site += x[i] * b.g.stride[i];
   BNode<D> nd;
   bnode_prepare<D, KIND>(b, x, nd);
   const int sgn = h ? -1 : 1;
 #pragma unroll
   for (int k = 0; k < Q; ++k)
-    if (L.e[k][0] == sgn) xb[t * J + xface_link<D>(k, sgn)] = bnode_data<D, KIND>(b, nd, k);
+    if (L.e[k][0] == sgn) xb[t * J + xface_link<D>(k, sgn)] = bnode_unknown<D, KIND, false>(b, nd, k, site);
 }
 
 // Forward step of a Dirichlet box (FP64, constant R), whole x-rows through the interior: the interior
 // lanes are those of k_step_fp64; the two face lanes of a row (x_1 = 0 or n_1 - 1, the other
 // coordinates interior) take each unknown population (e_k,1 = +1 on the low face, -1 on the high face)
-// from the data of k_xface_data (half-way: minus f*_kbar at the node) in the same load instruction as
+// from k_xface_data (which also subtracts the half-way scheme's f*_kbar) in the same load instruction as
 // the row's pulled populations, and collide with the row. The values are those of the boundary-node
 // kernel, bit for bit. Keeping these nodes in their rows avoids the boundary kernel's accesses strided
 // by n_1, which wasted most of a sector per population read and forced a fill of every partially
 // written sector.
-template <int D, int MODE, int KIND>
+template <int D, int MODE>
 __global__ void __launch_bounds__(LHE_STEP_THREADS) k_step_box(const StepArgs a, const double *__restrict__ xb) {
   constexpr Lattice<D> L{};
   constexpr int Q = Lattice<D>::Q;
@@ -77,7 +81,6 @@ __global__ void __launch_bounds__(LHE_STEP_THREADS) k_step_box(const StepArgs a,
     const bool unknown = face != 0 && L.e[k][0] == face;
     const int j = L.e[k][0] == 1 ? xface_link<D>(k, 1) : xface_link<D>(k, -1);
     f[k] = __ldg(unknown ? rec + j : src + k * S + source_site<D, false>(L, k, site, om, op));
-    if (KIND == 2 && L.e[k][0] != 0 && unknown) f[k] = f[k] - __ldg(src + L.opp[k] * S + site);
   }
   const double psi = MODE == kModeS2 ? fixed_moment_sum<Q, 1>(f) + a.dtR
                                      : fma(a.sig, fixed_moment_sum<Q, 0>(f), a.rho_dtR);
@@ -100,11 +103,8 @@ static cudaError_t step_box_d(int kind, const StepArgs &a, const BoundaryArgs &b
   const int threads = LHE_STEP_THREADS;
   const unsigned blocks = (unsigned)((a.nwork + threads - 1) / threads);
   const double *cxb = xb;
-  if (a.s == 2.0)
-    return kind == 1 ? launch_kernel(k_step_box<D, kModeS2, 1>, blocks, threads, 0, st, false, a, cxb)
-                     : launch_kernel(k_step_box<D, kModeS2, 2>, blocks, threads, 0, st, false, a, cxb);
-  return kind == 1 ? launch_kernel(k_step_box<D, kModeGeneral, 1>, blocks, threads, 0, st, false, a, cxb)
-                   : launch_kernel(k_step_box<D, kModeGeneral, 2>, blocks, threads, 0, st, false, a, cxb);
+  if (a.s == 2.0) return launch_kernel(k_step_box<D, kModeS2>, blocks, threads, 0, st, false, a, cxb);
+  return launch_kernel(k_step_box<D, kModeGeneral>, blocks, threads, 0, st, false, a, cxb);
 }
 
 cudaError_t launch_step_box_fp64(int d, int kind, const StepArgs &a, const BoundaryArgs &b, double *xb, int64_t nrows,

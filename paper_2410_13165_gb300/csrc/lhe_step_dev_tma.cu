@@ -156,7 +156,10 @@ __device__ __forceinline__ void issue_tile(const StepArgs &a, const DevTmaPlan &
 
 }  // namespace
 
-template <bool ADJ, bool S2>
+// NXC: the row length n_1 when it is fixed at compile time (rows of 128 or 256 nodes, tiles of 512
+// nodes: R = 512 / NXC), so that the node index of a unit splits into row and x without a runtime
+// division and the shared-memory offsets fold into constants; 0 for any other row length.
+template <bool ADJ, bool S2, int NXC>
 __global__ void __launch_bounds__(kTmaThreads, 1) k_step_dev3_tma(const StepArgs a, const DevTmaPlan p) {
   constexpr Lattice<3> L{};
   constexpr int Q = Lattice<3>::Q;
@@ -212,6 +215,10 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_step_dev3_tma(const StepArgs
   }
 
   // consumer warps
+  // (the row length and tile height, constants where NXC fixes them, else read from the plan at each
+  // use, so that the generic instantiation compiles as if NXC did not exist)
+#define LHE_NX (NXC ? NXC : p.nx)
+#define LHE_TILE_R (NXC ? 512 / NXC : p.R)
   const int sgn = ADJ ? -1 : 1;
   const int64_t S = a.g.S;
   const float oms = (float)a.oms;
@@ -227,33 +234,33 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_step_dev3_tma(const StepArgs
     float *__restrict__ dst = static_cast<float *>(a.dst);
     float2 *__restrict__ phi_dst = a.phi_dst;
     const int z = t.z;
-    const int y0 = t.ty * p.R;
+    const int y0 = t.ty * LHE_TILE_R;
     const float *G = reinterpret_cast<const float *>(smem + (size_t)s * p.stage_bytes);
     const float2 *P = reinterpret_cast<const float2 *>(smem + (size_t)s * p.stage_bytes + p.g_bytes);
     const double *X = reinterpret_cast<const double *>(smem + (size_t)s * p.stage_bytes + p.g_bytes + p.phi_bytes);
     // 32-node units of the tile, dealt to the consumer warps round robin over the whole sequence of
     // units of this CTA, so that warps which drew fewer units in one tile draw more in the next
-    const int units = (p.R * p.nx + 31) >> 5;
+    const int units = (LHE_TILE_R * LHE_NX + 31) >> 5;
     const int u0 = (int)(((unsigned)warp + (unsigned)kConsumerWarps - (unsigned)((i * units) % kConsumerWarps)) %
                          (unsigned)kConsumerWarps);
     for (int u = u0; u < units; u += kConsumerWarps) {
       const int idx = u * 32 + lane;
-      if (idx >= p.R * p.nx) break;
-      const int r = (int)p.nx_div.div((uint32_t)idx), x = idx - r * p.nx;
-      const int32_t site = x + p.nx * (y0 + r + p.ny * z);
-      const int xm = x == 0 ? p.nx - 1 : x - 1, xp = x == p.nx - 1 ? 0 : x + 1;
-      const float2 p0 = P[((p.R + 2) + r + 1) * p.nx + x];
+      if (idx >= LHE_TILE_R * LHE_NX) break;
+      const int r = NXC ? idx / NXC : (int)p.nx_div.div((uint32_t)idx), x = idx - r * LHE_NX;
+      const int32_t site = x + LHE_NX * (y0 + r + p.ny * z);
+      const int xm = x == 0 ? LHE_NX - 1 : x - 1, xp = x == LHE_NX - 1 ? 0 : x + 1;
+      const float2 p0 = P[((LHE_TILE_R + 2) + r + 1) * LHE_NX + x];
       float dl[Q], gk[Q];
       float accw = 0.0f, accg = 0.0f;
 #pragma unroll
       for (int k = 0; k < Q; ++k) {
         const int ex = sgn * L.e[k][0], ey = sgn * L.e[k][1], ez = sgn * L.e[k][2];
         const int sx = ex == 1 ? xm : (ex == -1 ? xp : x);
-        gk[k] = G[(k * p.R + r) * p.nx + sx];
+        gk[k] = G[(k * LHE_TILE_R + r) * LHE_NX + sx];
         if (k == 0) {
           dl[k] = 0.0f;
         } else {
-          const float2 pk = P[((1 - ez) * (p.R + 2) + r + 1 - ey) * p.nx + sx];
+          const float2 pk = P[((1 - ez) * (LHE_TILE_R + 2) + r + 1 - ey) * LHE_NX + sx];
           dl[k] = (pk.x - p0.x) + (pk.y - p0.y);
         }
         accw = fmaf(a.omega_f[k], dl[k], accw);
@@ -279,6 +286,8 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_step_dev3_tma(const StepArgs
     if (lane == 0) mbar_arrive(smem_u32(&empty[s]));
   }
 }
+#undef LHE_NX
+#undef LHE_TILE_R
 
 bool plan_dev3_tma(const Geom &g, int sms, DevTmaPlan &p) {
   if (g.d != 3) return false;
@@ -319,10 +328,21 @@ bool plan_dev3_tma(const Geom &g, int sms, DevTmaPlan &p) {
 cudaError_t prepare_dev3_tma(const DevTmaPlan &p) {
   const int bytes = p.NS * (int)p.stage_bytes;
   cudaError_t e;
-  if ((e = cudaFuncSetAttribute(k_step_dev3_tma<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes))) return e;
-  if ((e = cudaFuncSetAttribute(k_step_dev3_tma<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes))) return e;
-  if ((e = cudaFuncSetAttribute(k_step_dev3_tma<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes))) return e;
-  return cudaFuncSetAttribute(k_step_dev3_tma<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+#define LHE_SMEM(kernel) \
+  if ((e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes))) return e;
+  LHE_SMEM((k_step_dev3_tma<false, true, 0>)) LHE_SMEM((k_step_dev3_tma<false, false, 0>))
+  LHE_SMEM((k_step_dev3_tma<true, true, 0>)) LHE_SMEM((k_step_dev3_tma<true, false, 0>))
+  LHE_SMEM((k_step_dev3_tma<false, true, 128>)) LHE_SMEM((k_step_dev3_tma<false, false, 128>))
+  LHE_SMEM((k_step_dev3_tma<true, true, 128>)) LHE_SMEM((k_step_dev3_tma<true, false, 128>))
+  LHE_SMEM((k_step_dev3_tma<false, true, 256>)) LHE_SMEM((k_step_dev3_tma<false, false, 256>))
+#undef LHE_SMEM
+  return cudaSuccess;
+}
+
+template <int NXC>
+static auto pick_dev3_tma(bool adjoint, bool s2) {
+  return adjoint ? (s2 ? k_step_dev3_tma<true, true, NXC> : k_step_dev3_tma<true, false, NXC>)
+                 : (s2 ? k_step_dev3_tma<false, true, NXC> : k_step_dev3_tma<false, false, NXC>);
 }
 
 cudaError_t launch_step_dev3_tma(bool adjoint, const StepArgs &a, const DevTmaPlan &plan, cudaStream_t st) {
@@ -331,8 +351,12 @@ cudaError_t launch_step_dev3_tma(bool adjoint, const StepArgs &a, const DevTmaPl
   p.tx_bytes = p.g_bytes + p.phi_bytes + (with_x ? p.x_bytes : 0u);
   const size_t bytes = (size_t)p.NS * p.stage_bytes;
   const bool s2 = a.s == 2.0;
-  auto kernel = adjoint ? (s2 ? k_step_dev3_tma<true, true> : k_step_dev3_tma<true, false>)
-                        : (s2 ? k_step_dev3_tma<false, true> : k_step_dev3_tma<false, false>);
+  // Constant row lengths where they were measured faster: forward 128 and 256, adjoint 128 (the
+  // adjoint with constant rows of 256 was 6 % slower than with the runtime ones).
+  auto kernel = (p.nx == 128 && p.R == 4)                ? pick_dev3_tma<128>(adjoint, s2)
+                : (!adjoint && p.nx == 256 && p.R == 2)  ? (s2 ? k_step_dev3_tma<false, true, 256>
+                                                               : k_step_dev3_tma<false, false, 256>)
+                                                         : pick_dev3_tma<0>(adjoint, s2);
   return launch_kernel(kernel, p.grid, kTmaThreads, bytes, st, a.pdl != 0, a, p);
 }
 

@@ -3,7 +3,9 @@ asynchronous copies) against the register-pull kernel, bit for bit, and against 
 
 Both kernels evaluate the same per-node arithmetic in the same order, so every population, phi and
 dL/dR must agree exactly; the shapes cover tiles of one and several rows, wrap-around in y and z
-on grids of 3 rows, the maximum row length and extents the staged kernel does not take."""
+on grids of 3 rows, the maximum row length and extents the staged kernel does not take. Rows of 128
+and 256 nodes are run both where the kernel takes their length as a compile-time constant (tiles of
+4 and 2 rows) and where it does not (n_2 without such a divisor)."""
 import numpy as np
 import pytest
 
@@ -53,7 +55,7 @@ def _pair(n, tau, steps, R=0.0, Rf=None, seed=0):
 
 
 SHAPES = [(16, 12, 8), (32, 6, 5), (12, 20, 7), (64, 8, 3), (8, 3, 4), (128, 4, 3), (512, 3, 3), (4, 5, 6),
-          (20, 9, 5), (10, 6, 4), (576, 3, 3)]
+          (20, 9, 5), (10, 6, 4), (576, 3, 3), (128, 8, 5), (128, 6, 4), (256, 6, 3), (256, 3, 4)]
 
 
 @pytest.mark.parametrize("n", SHAPES)
@@ -66,10 +68,10 @@ def test_staged_step_is_bitwise_the_register_kernel(n, tau):
     assert torch.equal(phi_a, phi_b)
 
 
-def test_staged_step_with_sources_matches_the_oracle():
+@pytest.mark.parametrize("n", [(32, 12, 6), (128, 8, 3), (256, 4, 3)])
+def test_staged_step_with_sources_matches_the_oracle(n):
     import torch
 
-    n = (32, 12, 6)
     S = int(np.prod(n))
     Rf = 0.4 * np.sin(np.arange(S) * 0.013)
     (res, phi0, grad) = _pair(n, 0.8, 40, Rf=Rf, seed=3)
@@ -83,11 +85,11 @@ def test_staged_step_with_sources_matches_the_oracle():
     assert torch.equal(res[0][0], res[1][0])
 
 
+@pytest.mark.parametrize("n", [(32, 8, 6), (128, 8, 3), (256, 4, 3)])
 @pytest.mark.parametrize("tau", [0.5, 1.2])
-def test_staged_adjoint_is_bitwise_the_register_kernel(tau):
+def test_staged_adjoint_is_bitwise_the_register_kernel(n, tau):
     import torch
 
-    n = (32, 8, 6)
     phi0, grad = _problem(n, 9)
     rng = np.random.default_rng(10)
     target = rng.normal(size=int(np.prod(n)))

@@ -8,6 +8,10 @@ from arXiv:2410.13165 (see the citations in lhe_oracle.c).
 
 Layout: populations are numpy float64 arrays of shape (Q, S), S = prod(n), site index
 i_1 + n_1*(i_2 + ...) (x_1 fastest); the state is the PRE-collision population.
+
+Dirichlet data given as jets (Model.step_jets, Sec. 3.2) and their cotangent (Model.jet_grad, the
+transpose of the same formulas) are written in numpy here; jet_grad is pinned by central differences
+of step_jets (tests/test_oracle_jets.py).
 """
 from __future__ import annotations
 
@@ -274,6 +278,95 @@ class Model:
             cur, nxt = nxt, cur
         return cur
 
+    def _jet_links(self) -> dict:
+        """The unknown populations of a Dirichlet box (Sec. 3.2): every (site, link k) whose pull source
+        site - e_k lies outside the box, site-major, links in the order of k; with c_k, the opposite link,
+        the weights, and the position of each derivative tuple in a jet (orders 0..3 in (t, x_1..x_d),
+        tuples non-decreasing, by length then lexicographic)."""
+        import itertools
+
+        d, S, Q = self.d, self.S, self.Q
+        pos, j = {}, 0
+        for q in range(4):
+            for tup in itertools.combinations_with_replacement(range(d + 1), q):
+                pos[tup] = j
+                j += 1
+        idx = np.stack(np.unravel_index(np.arange(S), self.n[::-1])[::-1])  # (d, S), x_1 fastest
+        sites, links = [], []
+        for site in range(S):
+            for k in range(Q):
+                src = idx[:, site] - self.e[k]
+                if np.any(src < 0) or np.any(src >= np.asarray(self.n)):
+                    sites.append(site)
+                    links.append(k)
+        sites, links = np.asarray(sites, dtype=np.int64), np.asarray(links, dtype=np.int64)
+        kb = np.array([int(np.nonzero(np.all(self.e == -self.e[k], axis=1))[0][0]) for k in links], dtype=np.int64)
+        return {"pos": pos, "jlen": j, "sites": sites, "links": links, "ck": self.c * self.e[links].astype(np.float64),
+                "kb": kb, "wk": self.omega[links], "wkb": self.omega[kb]}
+
+    def _dir_deriv(self, jl, J, p, q):
+        """d_t^q (c_k . grad)^p phi from the jets J (U, jlen) of the unknown populations, summed over
+        ordered spatial tuples."""
+        import itertools
+
+        ck, pos = jl["ck"], jl["pos"]
+        out = np.zeros(len(jl["links"]))
+        for sp in itertools.product(range(1, self.d + 1), repeat=p):
+            w = np.ones(len(jl["links"]))
+            for i in sp:
+                w = w * ck[:, i - 1]
+            out += w * J[:, pos[tuple(sorted((0,) * q + sp))]]
+        return out
+
+    def _dir_deriv_T(self, jl, g, p, q):
+        """Transpose of _dir_deriv: the (U, jlen) cotangent of the jets for the cotangent g (U,) of
+        d_t^q (c_k . grad)^p phi."""
+        import itertools
+
+        ck, pos = jl["ck"], jl["pos"]
+        G = np.zeros((len(jl["links"]), jl["jlen"]))
+        for sp in itertools.product(range(1, self.d + 1), repeat=p):
+            w = np.ones(len(jl["links"]))
+            for i in sp:
+                w = w * ck[:, i - 1]
+            G[:, pos[tuple(sorted((0,) * q + sp))]] += w * g
+        return G
+
+    def jet_grad(self, lam):
+        """Cotangent of the Dirichlet jets of one step (the transpose of the map from jets to unknown
+        populations in step_jets, Eq. (bun1) / Eq. (bun2)). lam = dL/df (Q, S) of the pre-collision
+        state that the step produced, so the cotangent of each unknown population's value is
+        lam_k(site). The R terms and -f*_kbar do not depend on the jets. Returns (points (P, d),
+        grad (P, jlen)): full-way one point per boundary node (ascending site), the sum over its
+        unknown links; half-way one point per unknown population, at x - c_k dt/2, in the order of
+        _jet_links."""
+        jl = self._jet_links()
+        sites, links, wk, wkb = jl["sites"], jl["links"], jl["wk"], jl["wkb"]
+        dt = self.dt
+        g = np.asarray(lam, dtype=np.float64).reshape(self.Q, self.S)[links, sites]
+        T = lambda coef, p, q: self._dir_deriv_T(jl, coef * g, p, q)  # noqa: E731
+        X = self.coords()
+        if self.bc == "fullway":
+            G = T(wk, 0, 0)
+            if self.bc_order >= 3:
+                G = G - T(0.5 * dt * wk, 1, 0) - T(0.5 * dt * wk, 0, 1)
+            if self.bc_order >= 4:
+                G = G + T(dt ** 3 / 8.0 * wk, 1, 2) + T(dt ** 3 / 8.0 * wk, 2, 1) \
+                    + T(dt ** 3 / 24.0 * wk, 0, 3) + T(dt ** 3 / 24.0 * wk, 3, 0)
+            nodes, inv = np.unique(sites, return_inverse=True)
+            out = np.zeros((len(nodes), jl["jlen"]))
+            np.add.at(out, inv, G)
+            return X[:, nodes].T.copy(), out
+        wsum, wdif = wk + wkb, wk - wkb
+        G = T(wsum, 0, 0)
+        if self.bc_order >= 2:
+            G = G + T(0.5 * dt * wsum, 0, 1)
+        if self.bc_order >= 3:
+            G = G - T(dt * dt / 8.0 * wsum, 2, 0) - T(dt * dt / 4.0 * wdif, 1, 1)
+        if self.bc_order >= 4:
+            G = G - T(dt ** 3 / 8.0 * wdif, 1, 2) - T(dt ** 3 / 16.0 * wsum, 2, 1) - T(dt ** 3 / 24.0 * wsum, 0, 3)
+        return (X[:, sites].T - 0.5 * dt * jl["ck"]).copy(), G
+
     def step_jets(self, f, n0, nsteps, jet_fn, Rfield_fn=None) -> np.ndarray:
         """Dirichlet steps with the boundary data given as jets of phi: jet_fn(points (P, d), t)
         returns (P, J) arrays of every derivative of order 0..3 in (t, x_1..x_d), ordered by length
@@ -285,38 +378,14 @@ class Model:
         data: full-way t_{n+1} (Rfield_fn(n + 1)), half-way t_n (Rfield_fn(n))."""
         if self.bc == "periodic":
             raise ValueError("jets are Dirichlet data")
-        import itertools
-
-        d, S, Q = self.d, self.S, self.Q
-        pos, j = {}, 0
-        for q in range(4):
-            for tup in itertools.combinations_with_replacement(range(d + 1), q):
-                pos[tup] = j
-                j += 1
+        S = self.S
+        jl = self._jet_links()
+        sites, links, ck, kb, wk, wkb = jl["sites"], jl["links"], jl["ck"], jl["kb"], jl["wk"], jl["wkb"]
         X = self.coords()
-        idx = np.stack(np.unravel_index(np.arange(S), self.n[::-1])[::-1])  # (d, S), x_1 fastest
-        sites, links = [], []
-        for site in range(S):
-            for k in range(Q):
-                src = idx[:, site] - self.e[k]
-                if np.any(src < 0) or np.any(src >= np.asarray(self.n)):
-                    sites.append(site)
-                    links.append(k)
-        sites, links = np.asarray(sites, dtype=np.int64), np.asarray(links, dtype=np.int64)
-        ck = self.c * self.e[links].astype(np.float64)      # (U, d)
         dt = self.dt
-        kb = np.array([int(np.nonzero(np.all(self.e == -self.e[k], axis=1))[0][0]) for k in links], dtype=np.int64)
-        wk, wkb = self.omega[links], self.omega[kb]
 
         def dir_deriv(J, p, q):
-            """d_t^q (c_k . grad)^p phi from the jets J (U, J), summed over ordered spatial tuples."""
-            out = np.zeros(len(links))
-            for sp in itertools.product(range(1, d + 1), repeat=p):
-                w = np.ones(len(links))
-                for i in sp:
-                    w = w * ck[:, i - 1]
-                out += w * J[:, pos[tuple(sorted((0,) * q + sp))]]
-            return out
+            return self._dir_deriv(jl, J, p, q)
 
         w = OrcWave()  # no wave data: the unknown populations are replaced below
         cur = np.ascontiguousarray(f, dtype=np.float64).copy()

@@ -118,3 +118,77 @@ def test_manufactured_solution_with_a_varying_source():
         errs.append(float(np.sqrt(np.mean((m.phi(f) - W.sine_product_value(X, steps * m.dt)) ** 2))))
     rates = [np.log2(x / y) for x, y in zip(errs, errs[1:])]
     assert all(r > 0.8 for r in rates), (errs, rates)
+
+
+def _jet_problem(d, bc, order, T, seed):
+    """Small Dirichlet box, random state and random jets for T steps (oracle point order)."""
+    rng = np.random.default_rng(seed)
+    n = (6 if d == 2 else 4) if bc == "fullway" else (5 if d == 2 else 4)
+    u = (0.1, -0.05, 0.08)[:d] if bc == "fullway" else (0.01, -0.02, 0.015)[:d]
+    m = O.Model(d, [n] * d, 0.0, 1.0, u, tau=0.8, R=0.3, bc=bc, bc_order=order)
+    pts, _ = m.jet_grad(np.zeros((m.Q, m.S)))
+    key = {tuple(np.round(p / m.dx * 2).astype(int)): i for i, p in enumerate(pts)}
+    f0 = rng.normal(size=(m.Q, m.S))
+    jets = rng.normal(size=(T, len(pts), (d + 4) * (d + 3) * (d + 2) // 6))  # C(d + 4, 3) derivatives
+    target = rng.normal(size=m.S)
+    return m, pts, key, f0, jets, target
+
+
+def _jet_loss(m, key, f0, jets, target):
+    T = jets.shape[0]
+    off = 1 if m.bc == "fullway" else 0
+
+    def jet_fn(P, t):
+        n = int(round(t / m.dt)) - off
+        if m.bc == "halfway":  # one point per unknown population, in the order of jet_grad (mid-link
+            return jets[n]     # points of diagonal links of neighbouring nodes coincide)
+        rows = [key[tuple(np.round(p / m.dx * 2).astype(int))] for p in P]  # full-way: per node
+        return jets[n][rows]
+
+    f = m.step_jets(f0, 0, T, jet_fn)
+    r = m.phi(f) - target
+    return 0.5 * float(np.dot(r, r)), r
+
+
+@pytest.mark.parametrize("bc,order", [("fullway", 1), ("fullway", 3), ("fullway", 4), ("halfway", 1), ("halfway", 2),
+                                      ("halfway", 3), ("halfway", 4)])
+@pytest.mark.parametrize("d", [2, 3])
+def test_jet_gradient_matches_central_differences(d, bc, order):
+    """The adjoint jet cotangent (Model.jet_grad after each Model.adjoint_step, from dL/dphi_T) against
+    central differences of the loss 1/2 |phi_T - target|^2 of the forward jet path along random
+    directions. The loss is quadratic in the jets, so the differences are exact up to rounding."""
+    T = 3
+    m, pts, key, f0, jets, target = _jet_problem(d, bc, order, T, seed=100 + 10 * d + order)
+    _, r = _jet_loss(m, key, f0, jets, target)
+    lam = np.ascontiguousarray(np.broadcast_to(r, (m.Q, m.S)).copy())  # dL/df_k = dL/dphi (phi = sum_k f_k)
+    grads = [None] * T
+    for n in range(T - 1, -1, -1):
+        p, grads[n] = m.jet_grad(lam)
+        assert np.array_equal(p, pts)
+        lam = m.adjoint_step(lam)
+    G = np.stack(grads)
+    assert np.any(G != 0.0)
+    rng = np.random.default_rng(7)
+    for _ in range(3):
+        v = rng.normal(size=jets.shape)
+        lp, _ = _jet_loss(m, key, f0, jets + v, target)
+        lm, _ = _jet_loss(m, key, f0, jets - v, target)
+        fd = (lp - lm) / 2.0
+        an = float(np.sum(G * v))
+        assert abs(fd - an) <= 1e-11 * max(abs(fd), abs(lp), abs(lm)), (fd, an)
+
+
+def test_jet_gradient_entries_by_brute_force():
+    """Every entry of the jet cotangent of one full-way and one half-way step on a 2D box, by central
+    differences of the one-step loss along each unit direction."""
+    for bc in ("fullway", "halfway"):
+        m, pts, key, f0, jets, target = _jet_problem(2, bc, 4, 1, seed=5)
+        _, r = _jet_loss(m, key, f0, jets, target)
+        lam = np.ascontiguousarray(np.broadcast_to(r, (m.Q, m.S)).copy())
+        _, G = m.jet_grad(lam)
+        for i in range(0, G.shape[0], 3):
+            for j in range(G.shape[1]):
+                e = np.zeros_like(jets)
+                e[0, i, j] = 1.0
+                fd = (_jet_loss(m, key, f0, jets + e, target)[0] - _jet_loss(m, key, f0, jets - e, target)[0]) / 2.0
+                assert abs(fd - G[i, j]) <= 1e-11 * (1.0 + abs(fd)), (bc, i, j, fd, G[i, j])

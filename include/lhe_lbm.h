@@ -268,7 +268,8 @@ LHE_API lhe_status lhe_lbm_set_state(lhe_lbm *lbm, const void *buf, int64_t step
  * buffers on first use. Dirichlet boxes (FP64 only; LHE_ERR_STATE for FP32_DEV): the transpose of
  * the boundary schemes drops the populations that leave the box (full-way, Eq. (bun1)) or returns
  * them, negated, to the opposite link of the same node (half-way, Eq. (bun2)); the boundary data
- * enter additively and have no adjoint here, and dL/dR(x) is not available (constant R). */
+ * enter additively: lhe_lbm_adjoint_jet_grad gives their cotangent per step as jets. dL/dR(x) is not
+ * available on Dirichlet boxes (constant R). */
 LHE_API lhe_status lhe_lbm_adjoint_seed(lhe_lbm *lbm, const double *dL_dphiT_dev);
 LHE_API lhe_status lhe_lbm_adjoint_step(lhe_lbm *lbm, int64_t n);
 /* dL/dphi0 (S doubles), dL/d(grad phi0) (d*S doubles, only meaningful when lhe_lbm_init got an
@@ -276,6 +277,19 @@ LHE_API lhe_status lhe_lbm_adjoint_step(lhe_lbm *lbm, int64_t n);
  * boxes, else LHE_ERR_ARG). When init used the finite-difference gradient, its transpose is folded
  * into dL/dphi0. */
 LHE_API lhe_status lhe_lbm_adjoint_grads(lhe_lbm *lbm, double *dL_dphi0_dev, double *dL_dgrad_dev, double *dL_dR_dev);
+
+/* Cotangent of the Dirichlet data of one step, as jets (Sec. 3.2; the transpose of the map from jets
+ * to unknown populations of lhe_lbm_set_boundary_jet, Eq. (bun1) / Eq. (bun2)). When the adjoint
+ * state is dL/df(t_m) (after lhe_lbm_adjoint_seed at t_T and T - m adjoint steps), dL_djet_dev
+ * (device, P * LHE_JET_LEN(d) doubles, point-major, the points and derivative order of
+ * lhe_lbm_boundary_points and lhe_lbm_set_boundary_jet) receives dL/d(jet) of the data of the step
+ * t_{m-1} -> t_m: full-way the jets at the boundary nodes and t_m, half-way those at the mid-link
+ * points and t_{m-1}. Call it before each lhe_lbm_adjoint_step(lbm, 1) to collect every step's. It
+ * does not depend on whether the forward step took jets or lhe_lbm_set_boundary_wave's family: the
+ * scheme is the same linear map of its data. Asynchronous on the handle's stream; the adjoint state is
+ * unchanged. Errors: LHE_ERR_STATE on a periodic box or before lhe_lbm_adjoint_seed, LHE_ERR_ARG for
+ * NULL, LHE_ERR_CUDA. */
+LHE_API lhe_status lhe_lbm_adjoint_jet_grad(lhe_lbm *lbm, double *dL_djet_dev);
 
 /* ---------------- stability maps (Sec. 4) ----------------
  * For npoints velocities sigma = u/c (sigma_host: npoints*d doubles, point-major, host memory):

@@ -213,6 +213,17 @@ class LBM:
                                    None if gR is None else gR.data_ptr())
         return gphi, ggrad, gR
 
+    def adjoint_jet_grad(self, out=None):
+        """dL/d(jet) of the Dirichlet data of the step that the next adjoint_step(1) reverses, as a
+        (P, jet_len(d)) float64 tensor at boundary_points() (lhe_lbm_adjoint_jet_grad)."""
+        P = len(self.boundary_points()[0])
+        JL = jet_len(self.d)
+        if out is None:
+            out = self._torch.empty((P, JL), dtype=self._torch.float64, device=self.device)
+        self._stream()
+        _abi.lhe_lbm_adjoint_jet_grad(self.h, self._ptr(out, P * JL, "out"))
+        return out
+
     def close(self):
         if getattr(self, "h", None):
             _abi.lhe_lbm_destroy(self.h)

@@ -31,7 +31,7 @@ EXPORTS = [
     "lhe_lbm_set_boundary_wave", "lhe_lbm_step", "lhe_lbm_macro", "lhe_lbm_diagnostics", "lhe_lbm_get_state",
     "lhe_lbm_set_state", "lhe_lbm_adjoint_seed", "lhe_lbm_adjoint_step", "lhe_lbm_adjoint_grads",
     "lhe_lbm_diagnostics_noalloc", "lhe_lbm_stability_map", "lhe_lbm_boundary_points", "lhe_lbm_set_boundary_jet",
-    "lhe_lbm_set_source",
+    "lhe_lbm_adjoint_jet_grad", "lhe_lbm_set_source",
 ]
 
 
@@ -110,6 +110,7 @@ def load(path: str | None = None):
         "lhe_lbm_adjoint_seed": (st, [_H, _D]),
         "lhe_lbm_adjoint_step": (st, [_H, ctypes.c_int64]),
         "lhe_lbm_adjoint_grads": (st, [_H, _D, _D, _D]),
+        "lhe_lbm_adjoint_jet_grad": (st, [_H, _D]),
         "lhe_lbm_diagnostics_noalloc": (st, [ctypes.POINTER(lhe_lbm_params), _D, _D, _D]),
         "lhe_lbm_stability_map": (st, [ctypes.POINTER(lhe_lbm_params), _D, ctypes.c_int64, ctypes.c_int32, _D, _D]),
     }
@@ -239,6 +240,10 @@ def lhe_lbm_adjoint_step(h, n: int) -> None:
 
 def lhe_lbm_adjoint_grads(h, gphi0_ptr: int, ggrad_ptr: int | None, gR_ptr: int | None) -> None:
     check(load().lhe_lbm_adjoint_grads(h, gphi0_ptr, ggrad_ptr, gR_ptr), h)
+
+
+def lhe_lbm_adjoint_jet_grad(h, out_ptr: int) -> None:
+    check(load().lhe_lbm_adjoint_jet_grad(h, out_ptr), h)
 
 
 def lhe_lbm_diagnostics_noalloc(p: lhe_lbm_params, pop_ptr: int, R_ptr: int | None, out_ptr: int) -> None:

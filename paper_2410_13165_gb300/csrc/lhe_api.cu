@@ -763,19 +763,12 @@ lhe_status lhe_lbm_boundary_points(const lhe_lbm *l, double *xyz_host, int64_t *
   return LHE_OK;
 }
 
-lhe_status lhe_lbm_set_boundary_jet(lhe_lbm *l, const double *jet_dev) {
-  if (lhe_status s = check_handle(l)) return s;
-  if (l->p.bc == LHE_BC_PERIODIC) return fail(l, LHE_ERR_STATE, "boundary data on a periodic box");
-  if (!jet_dev) return fail(l, LHE_ERR_ARG, "jet is NULL");
-  if (lhe_status st = check_pipeline(l)) return st;
-  const int d = l->p.d;
-  if (!l->broff) {
-    LHE_CK(l, cudaMalloc((void **)&l->broff, sizeof(int32_t) * l->broff_host.size()));
-    LHE_CK(l, cudaMemcpy(l->broff, l->broff_host.data(), sizeof(int32_t) * l->broff_host.size(), cudaMemcpyHostToDevice));
-    LHE_CK(l, cudaMalloc((void **)&l->brec, sizeof(double) * (size_t)std::max<int64_t>(l->nrec, 1)));
-  }
-  // position of each derivative in a jet: orders 0..3, index tuples v1 <= .. <= vq in lexicographic
-  // order (v = 0: t, v = i: x_i); the tables list every ordering of a tuple
+}  // extern "C"
+
+// Position of each derivative in a boundary jet: orders 0..3, index tuples v1 <= .. <= vq in
+// lexicographic order (v = 0: t, v = i: x_i); entries [a*36 + b*6 + c] (order 3) and [216 + a*6 + b]
+// (order 2) list every ordering of a tuple.
+static std::vector<int16_t> jet_index_table(int d) {
   std::vector<int16_t> jidx(216 + 36, 0);
   int16_t pos = (int16_t)(1 + (d + 1));
   for (int a = 0; a <= d; ++a)
@@ -791,14 +784,48 @@ lhe_status lhe_lbm_set_boundary_jet(lhe_lbm *l, const double *jet_dev) {
         for (const auto &q : perm) jidx[q[0] * 36 + q[1] * 6 + q[2]] = pos;
         ++pos;
       }
+  return jidx;
+}
+
+// The per-node offsets of the unknown populations (device) and the record buffer, on first use.
+static lhe_status ensure_jet_buffers(lhe_lbm *l) {
+  if (l->broff) return LHE_OK;
+  LHE_CK(l, cudaMalloc((void **)&l->broff, sizeof(int32_t) * l->broff_host.size()));
+  LHE_CK(l, cudaMemcpy(l->broff, l->broff_host.data(), sizeof(int32_t) * l->broff_host.size(), cudaMemcpyHostToDevice));
+  LHE_CK(l, cudaMalloc((void **)&l->brec, sizeof(double) * (size_t)std::max<int64_t>(l->nrec, 1)));
+  return LHE_OK;
+}
+
+extern "C" {
+
+lhe_status lhe_lbm_set_boundary_jet(lhe_lbm *l, const double *jet_dev) {
+  if (lhe_status s = check_handle(l)) return s;
+  if (l->p.bc == LHE_BC_PERIODIC) return fail(l, LHE_ERR_STATE, "boundary data on a periodic box");
+  if (!jet_dev) return fail(l, LHE_ERR_ARG, "jet is NULL");
+  if (lhe_status st = check_pipeline(l)) return st;
+  if (lhe_status st = ensure_jet_buffers(l)) return st;
   BoundaryArgs b = boundary_args(l);
   b.roff = l->broff;  // the kernel writes l->brec; b.rec stays null (the data are being formed)
   // the schemes' R terms (a source varying in time): full-way at the new time t_{n+1} (the source of
   // this step's collision), half-way at t_n (the source of the collision of f*_kbar)
   b.Rfield = l->p.bc == LHE_BC_FULLWAY ? next_source(l) : l->Rfield;
-  LHE_CK(l, launch_jet_records(d, l->p.bc, b, jet_dev, jidx.data(), l->brec, l->stream));
+  LHE_CK(l, launch_jet_records(l->p.d, l->p.bc, b, jet_dev, jet_index_table(l->p.d).data(), l->brec, l->stream));
   l->jet_mode = true;
   l->jet_ready = true;
+  return LHE_OK;
+}
+
+lhe_status lhe_lbm_adjoint_jet_grad(lhe_lbm *l, double *out) {
+  if (lhe_status s = check_handle(l)) return s;
+  if (l->p.bc == LHE_BC_PERIODIC) return fail(l, LHE_ERR_STATE, "boundary jets on a periodic box");
+  if (!out) return fail(l, LHE_ERR_ARG, "dL/djet is NULL");
+  if (!l->adj_ready) return fail(l, LHE_ERR_STATE, "lhe_lbm_adjoint_jet_grad before lhe_lbm_adjoint_seed");
+  if (lhe_status st = check_pipeline(l)) return st;
+  if (lhe_status st = ensure_jet_buffers(l)) return st;
+  BoundaryArgs b = boundary_args(l);
+  b.roff = l->broff;
+  b.src = l->adj[l->acur];
+  LHE_CK(l, launch_jet_grad(l->p.d, l->p.bc, b, jet_index_table(l->p.d).data(), out, l->stream));
   return LHE_OK;
 }
 

@@ -227,6 +227,115 @@ cudaError_t launch_jet_records(int d, int kind, const BoundaryArgs &a, const dou
   }
 }
 
+// Cotangent of the jets of one Dirichlet step (lhe_lbm_adjoint_jet_grad): the transpose of
+// k_jet_records. a.src holds the adjoint state rho_k(x) = omega_k dL/df_k(x) of the pre-collision
+// populations that the step produced, so the cotangent of an unknown population's value is
+// rho_k / omega_k (the R terms and the half-way -f*_kbar do not depend on the jets). Full-way: one row
+// per boundary node, summed over its unknown links (omega_k times the cotangent is rho_k); half-way:
+// one row per unknown population, w+ and w- times rho_k / omega_k. Each thread owns the rows of its
+// node and zeroes them first.
+template <int D, int KIND>
+__global__ void __launch_bounds__(128) k_jet_grad(const BoundaryArgs a, const JetIndex J, double *__restrict__ out) {
+  constexpr Lattice<D> L{};
+  constexpr int Q = Lattice<D>::Q;
+  constexpr int JL = (D + 4) * (D + 3) * (D + 2) / 6;
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= a.nsites) return;
+  const int32_t site = a.sites[t];
+  int x[D];
+  {
+    uint32_t r = (uint32_t)site;
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      if (i == D - 1) {
+        x[i] = (int)r;
+      } else {
+        const uint32_t q = a.g.dv[i].div(r);
+        x[i] = (int)(r - q * (uint32_t)a.g.n[i]);
+        r = q;
+      }
+    }
+  }
+  const double *__restrict__ rho = static_cast<const double *>(a.src);
+  const int64_t S = a.g.S;
+  const int32_t r0 = a.roff[t];
+  const int P = a.order;
+  const double dt = a.dt;
+  if (KIND == 1)
+    for (int e = 0; e < JL; ++e) out[t * JL + e] = 0.0;
+  int ju = 0;
+  for (int k = 0; k < Q; ++k) {
+    bool inside = true;
+    for (int i = 0; i < D; ++i) {
+      const int xs = x[i] - L.e[k][i];
+      if (xs < 0 || xs >= a.g.n[i]) inside = false;
+    }
+    if (inside) continue;
+    double *g = out + (size_t)(KIND == 1 ? t : r0 + ju) * JL;
+    double w[D + 1];  // weights of the variables in (d_t + c.grad): 1 for t, c_i for x_i
+    w[0] = 1.0;
+    for (int i = 0; i < D; ++i) w[i + 1] = a.c * L.e[k][i];
+    const double rk = rho[k * S + site];
+    if (KIND == 1) {
+      g[0] += rk;
+      if (P >= 3)
+        for (int v = 0; v <= D; ++v) g[1 + v] -= 0.5 * dt * w[v] * rk;
+      if (P >= 4) {
+        const double c3 = dt * dt * dt / 24.0 * rk;
+        for (int p0 = 0; p0 <= D; ++p0)
+          for (int p1 = 0; p1 <= D; ++p1)
+            for (int p2 = 0; p2 <= D; ++p2) {
+              const double ww = w[p0] * w[p1] * w[p2];
+              if (ww != 0.0) g[J.i3[p0 * 36 + p1 * 6 + p2]] += ww * c3;
+            }
+      }
+    } else {
+      for (int e = 0; e < JL; ++e) g[e] = 0.0;
+      const int kb = L.opp[k];
+      const double lam = rk / a.omega[k];
+      const double wp = (a.omega[k] + a.omega[kb]) * lam, wm = (a.omega[k] - a.omega[kb]) * lam;
+      g[0] = wp;
+      if (P >= 2) g[1] += 0.5 * dt * wp;
+      if (P >= 3)
+        for (int p0 = 1; p0 <= D; ++p0) {
+          g[J.i2[p0 * 6]] -= dt * dt / 4.0 * wm * w[p0];
+          for (int p1 = 1; p1 <= D; ++p1) g[J.i2[p0 * 6 + p1]] -= dt * dt / 8.0 * wp * w[p0] * w[p1];
+        }
+      if (P >= 4) {
+        g[J.i3[0]] -= dt * dt * dt / 24.0 * wp;
+        for (int p0 = 1; p0 <= D; ++p0) {
+          g[J.i3[p0 * 36]] -= dt * dt * dt / 8.0 * wm * w[p0];
+          for (int p1 = 1; p1 <= D; ++p1) g[J.i3[p0 * 36 + p1 * 6]] -= dt * dt * dt / 16.0 * wp * w[p0] * w[p1];
+        }
+      }
+    }
+    ++ju;
+  }
+}
+
+template <int D>
+static cudaError_t jet_grad_d(int kind, const BoundaryArgs &a, const JetIndex &J, double *out, cudaStream_t st) {
+  if (a.nsites <= 0) return cudaSuccess;
+  const unsigned blocks = (unsigned)((a.nsites + 127) / 128);
+  if (kind == 1) k_jet_grad<D, 1><<<blocks, 128, 0, st>>>(a, J, out);
+  else k_jet_grad<D, 2><<<blocks, 128, 0, st>>>(a, J, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_jet_grad(int d, int kind, const BoundaryArgs &a, const int16_t *jidx, double *out, cudaStream_t st) {
+  JetIndex J;
+  for (int i = 0; i < 216; ++i) J.i3[i] = jidx[i];
+  for (int i = 0; i < 36; ++i) J.i2[i] = jidx[216 + i];
+  switch (d) {
+    case 1: return jet_grad_d<1>(kind, a, J, out, st);
+    case 2: return jet_grad_d<2>(kind, a, J, out, st);
+    case 3: return jet_grad_d<3>(kind, a, J, out, st);
+    case 4: return jet_grad_d<4>(kind, a, J, out, st);
+    case 5: return jet_grad_d<5>(kind, a, J, out, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 // Adjoint of a Dirichlet step at the boundary nodes (FP64), in the weighted variable
 // rho_k(x) = omega_k dL/df_k(x) of the pre-collision populations (the interior nodes use the bulk
 // adjoint kernel). Transposing the pull: mu_j(x) = omega_j dL/df*_j(x) = rho_j(x + e_j) where

@@ -170,6 +170,7 @@ cudaError_t launch_step_dev(int d, bool adjoint, bool interior, const StepArgs &
 cudaError_t launch_boundary(int d, int kind, bool dev, const BoundaryArgs &a, cudaStream_t st);
 cudaError_t launch_jet_records(int d, int kind, const BoundaryArgs &a, const double *jet, const int16_t *jidx,
                                double *rec, cudaStream_t st);
+cudaError_t launch_jet_grad(int d, int kind, const BoundaryArgs &a, const int16_t *jidx, double *out, cudaStream_t st);
 cudaError_t launch_step_box_fp64(int d, int kind, const StepArgs &a, const BoundaryArgs &b, double *xb, int64_t nrows,
                                  cudaStream_t st);
 cudaError_t launch_adjoint_boundary(int d, int kind, const BoundaryArgs &a, cudaStream_t st);

@@ -218,3 +218,110 @@ def test_a_source_field_needs_jets_on_dirichlet_boxes():
     sim.set_source(None)
     sim.step(1)  # constant R again: the wave data apply
     sim.close()
+
+
+def _adjoint_jet_grads(sim, seed, steps):
+    """dL/d(jet) of every step, newest first reversed to step order, from dL/dphi_T = seed."""
+    sim.adjoint_seed(_t(seed))
+    out = []
+    for _ in range(steps):
+        out.append(sim.adjoint_jet_grad().cpu().numpy())
+        sim.adjoint_step(1)
+    return out[::-1]
+
+
+def _oracle_jet_grads(m, seed, steps):
+    lam = np.ascontiguousarray(np.broadcast_to(np.asarray(seed).ravel(), (m.Q, m.S)).copy())
+    out = []
+    for _ in range(steps):
+        pts, g = m.jet_grad(lam)
+        out.append(g)
+        lam = m.adjoint_step(lam)
+    return pts, out[::-1]
+
+
+def _by_point(pts, g, dx):
+    """Rows summed per distinct point (half-way mid-link points of diagonal links of neighbouring
+    nodes coincide), keyed by the point in units of dx / 2."""
+    acc = {}
+    for p, row in zip(pts, g):
+        key = tuple(np.round(np.asarray(p) / dx * 2).astype(int))
+        acc[key] = acc.get(key, 0.0) + row
+    return acc
+
+
+@pytest.mark.parametrize("d,n,bc,order,tau", [
+    (2, 41, "fullway", 4, 0.5), (2, 40, "halfway", 4, 0.8), (2, 41, "fullway", 1, 0.8), (2, 20, "halfway", 2, 0.5),
+    (3, 11, "fullway", 3, 1.2), (3, 10, "halfway", 4, 0.5), (4, 6, "fullway", 4, 0.5), (4, 6, "halfway", 3, 0.8)])
+def test_adjoint_jet_grad_matches_the_oracle(d, n, bc, order, tau):
+    """The cotangent of every step's jets from a seeded dL/dphi_T against the oracle's transpose
+    (Model.jet_grad after Model.adjoint_step): full-way per boundary node, half-way per distinct
+    mid-link point; several blocks of boundary nodes. FP64 1e-12 relative."""
+    u = [0.1, 0.05, -0.08, 0.06][:d] if bc == "fullway" else [0.01, 0.02, -0.01, 0.015][:d]
+    steps = 4
+    rng = np.random.default_rng(17 + d + order)
+    m = O.Model(d, n, 0.0, 1.0, u, tau=tau, R=0.3, bc=bc, bc_order=order)
+    seed = rng.normal(size=m.S)
+    opts, og = _oracle_jet_grads(m, seed, steps)
+    sim = LBM(d, n, 0.0, 1.0, u=u, tau=tau, R=0.3, bc=bc, bc_order=order)
+    sim.init(_t(np.zeros(m.S)), _t(np.zeros(d * m.S)))
+    pts, _ = sim.boundary_points()
+    gg = _adjoint_jet_grads(sim, seed, steps)
+    sim.close()
+    assert len(pts) > 128 and gg[0].shape == (len(pts), jet_len(d)) and len(pts) == len(opts)
+    scale = max(np.max(np.abs(g)) for g in og)
+    for a, b in zip(gg, og):
+        A, B = _by_point(pts, a, m.dx), _by_point(opts, b, m.dx)
+        assert A.keys() == B.keys()
+        err = max(np.max(np.abs(A[k] - B[k])) for k in A)
+        assert err <= 1e-12 * scale, err
+
+
+@pytest.mark.parametrize("d,n,bc,order", [(2, 19, "fullway", 4), (2, 18, "halfway", 4), (3, 9, "fullway", 3),
+                                          (3, 8, "halfway", 3), (5, 5, "fullway", 4), (5, 4, "halfway", 4)])
+def test_adjoint_jet_grad_is_the_transpose_of_the_forward(d, n, bc, order):
+    """With phi0 = 0 and R = 0 the final field is linear in the jets V_n of the steps, so
+    <seed, phi_T(V)> = sum_n <dL/djet_n, V_n> for L = <seed, phi_T>; random V per row (one jet per
+    unknown population, coincident half-way points included)."""
+    import torch
+
+    u = [0.02, 0.04, 0.06, 0.08, 0.1][:d] if bc == "fullway" else [0.01, 0.02, 0.01, 0.02, 0.01][:d]
+    steps = 3
+    rng = np.random.default_rng(5 + d)
+    sim = LBM(d, n, 0.0, 1.0, u=u, tau=0.8, R=0.0, bc=bc, bc_order=order)
+    S = sim.S
+    sim.init(_t(np.zeros(S)), _t(np.zeros(d * S)))
+    P = len(sim.boundary_points()[0])
+    V = rng.normal(size=(steps, P, jet_len(d)))
+    for k in range(steps):
+        sim.set_boundary_jet(_t(V[k]))
+        sim.step(1)
+    seed = rng.normal(size=S)
+    lhs = float(np.dot(seed, sim.macro().cpu().numpy()))
+    G = _adjoint_jet_grads(sim, seed, steps)
+    rhs = float(sum(np.sum(g * v) for g, v in zip(G, V)))
+    sim.close()
+    torch.cuda.synchronize()
+    assert abs(lhs - rhs) <= 1e-12 * max(1.0, abs(lhs), float(sum(np.sum(np.abs(g * v)) for g, v in zip(G, V))))
+
+
+def test_adjoint_jet_grad_errors():
+    import torch
+
+    buf = torch.zeros(4096, dtype=torch.float64, device="cuda")
+    sim = LBM(2, 8, 0.0, 1.0, u=(0.1, 0.05), bc="fullway", bc_order=4)
+    sim.init(_t(np.zeros(64)), _t(np.zeros(128)))
+    with pytest.raises(LHEError):
+        _abi.lhe_lbm_adjoint_jet_grad(sim.h, buf.data_ptr())  # before adjoint_seed
+    sim.adjoint_seed(_t(np.ones(64)))
+    with pytest.raises(LHEError):
+        _abi.lhe_lbm_adjoint_jet_grad(sim.h, None)
+    g = sim.adjoint_jet_grad()
+    assert g.shape == (28, jet_len(2)) and bool(torch.isfinite(g).all())
+    sim.close()
+    per = LBM(2, 8, u=(0.1, 0.05))
+    per.init(_t(np.zeros(64)))
+    per.adjoint_seed(_t(np.zeros(64)))
+    with pytest.raises(LHEError):
+        _abi.lhe_lbm_adjoint_jet_grad(per.h, buf.data_ptr())  # periodic box
+    per.close()

@@ -325,3 +325,36 @@ def test_adjoint_jet_grad_errors():
     with pytest.raises(LHEError):
         _abi.lhe_lbm_adjoint_jet_grad(per.h, buf.data_ptr())  # periodic box
     per.close()
+
+
+@pytest.mark.parametrize("d,n,bc,order", [(2, 17, "fullway", 4), (2, 16, "halfway", 4), (3, 8, "halfway", 2)])
+def test_box_autograd_matches_central_differences(d, n, bc, order):
+    """LBMBoxFunction: phi_T of a Dirichlet box as a function of phi0, grad phi0 and every step's
+    jets; torch.autograd's gradients against central differences of the loss 1/2 |phi_T - target|^2
+    along random directions (exact up to rounding: the loss is quadratic in all three)."""
+    import torch
+    from paper_2410_13165_gb300.autograd import LBMBoxFunction
+
+    u = [0.1, 0.05, -0.08][:d] if bc == "fullway" else [0.01, 0.02, -0.01][:d]
+    T = 5
+    sim = LBM(d, n, 0.0, 1.0, u=u, tau=0.8, R=0.3, bc=bc, bc_order=order)
+    S, P, JL = sim.S, len(sim.boundary_points()[0]), jet_len(d)
+    rng = np.random.default_rng(31 + d)
+    cuda = lambda a, g=False: torch.tensor(a, dtype=torch.float64, device="cuda", requires_grad=g)  # noqa: E731
+    phi0, grad, jets = cuda(rng.normal(size=S), True), cuda(rng.normal(size=(d, S)), True), cuda(rng.normal(size=(T, P, JL)), True)
+    target = cuda(rng.normal(size=S))
+
+    def loss(a, b, c):
+        r = LBMBoxFunction.apply(a, b, c, sim) - target
+        return 0.5 * torch.dot(r, r)
+
+    loss(phi0, grad, jets).backward()
+    assert phi0.grad.shape == phi0.shape and grad.grad.shape == grad.shape and jets.grad.shape == jets.shape
+    with torch.no_grad():
+        for _ in range(3):
+            v = [cuda(rng.normal(size=tuple(x.shape))) for x in (phi0, grad, jets)]
+            lp = float(loss(phi0 + v[0], grad + v[1], jets + v[2]))
+            lm = float(loss(phi0 - v[0], grad - v[1], jets - v[2]))
+            an = float(sum(torch.sum(x.grad * w) for x, w in zip((phi0, grad, jets), v)))
+            assert abs((lp - lm) / 2.0 - an) <= 1e-11 * max(lp, lm, 1.0), ((lp - lm) / 2.0, an)
+    sim.close()

@@ -278,6 +278,28 @@ LHE_API lhe_status lhe_lbm_adjoint_step(lhe_lbm *lbm, int64_t n);
  * into dL/dphi0. */
 LHE_API lhe_status lhe_lbm_adjoint_grads(lhe_lbm *lbm, double *dL_dphi0_dev, double *dL_dgrad_dev, double *dL_dR_dev);
 
+/* The manufactured solution phi*(x, t) = A exp(-lambda t) prod_i sin(kappa_i x_i + theta_i) of
+ * phi_t + u . grad phi = R with its own source R(x, t) = -lambda phi* + sum_i u_i d_i phi*, which
+ * varies in x and t (kappa and theta: the first d entries are used). */
+typedef struct {
+  double A, lambda;
+  double kappa[LHE_MAX_DIM];
+  double theta[LHE_MAX_DIM];
+} lhe_sine_product;
+
+/* Dirichlet data and source from the manufactured solution *sp_host (copied), formed on the device.
+ * Every following lhe_lbm_step (any n) takes, for its step t_n -> t_{n+1}, the source R(x, t_{n+1}) of
+ * its collision and the boundary data of Eq. (bun1) (at t_{n+1}) or Eq. (bun2) (at t_n) exactly as
+ * lhe_lbm_set_boundary_jet would form them from the solution's jets at lhe_lbm_boundary_points, with
+ * the R terms at the boundary node (lhe_lbm_set_source). The solution separates, phi* = exp(-lambda t)
+ * P(x): this call forms the jets of P, the field R(x, t) exp(lambda t) and their records once
+ * (synchronising the stream; P * LHE_JET_LEN(d) doubles of scratch); each step scales them by
+ * exp(-lambda t). Initialise with lhe_lbm_init's R_dev = R(x, 0) so that the stored state carries the
+ * solution's source. lhe_lbm_set_boundary_wave, lhe_lbm_set_boundary_jet and lhe_lbm_set_source end
+ * it. Errors: LHE_ERR_STATE on a periodic box, LHE_ERR_ARG for NULL or non-finite parameters,
+ * LHE_ERR_OOM / LHE_ERR_CUDA. */
+LHE_API lhe_status lhe_lbm_set_boundary_sine_product(lhe_lbm *lbm, const lhe_sine_product *sp_host);
+
 /* Cotangent of the Dirichlet data of one step, as jets (Sec. 3.2; the transpose of the map from jets
  * to unknown populations of lhe_lbm_set_boundary_jet, Eq. (bun1) / Eq. (bun2)). When the adjoint
  * state is dL/df(t_m) (after lhe_lbm_adjoint_seed at t_T and T - m adjoint steps), dL_djet_dev

@@ -154,6 +154,20 @@ class LBM:
         self._stream()
         _abi.lhe_lbm_set_source(self.h, self._ptr(R, self.S, "R"))
 
+    def set_boundary_sine_product(self, A=1.0, lam=1.0, kappa=None, theta=None):
+        """Boundary data and source of phi* = A exp(-lam t) prod_i sin(kappa_i x_i + theta_i) (default
+        kappa_i = pi, theta_i = 0), formed on the device for every following step; initialise with
+        R(x, 0) of the same solution (lhe_lbm_set_boundary_sine_product)."""
+        import math
+
+        sp = _abi.lhe_sine_product()
+        sp.A, sp.lam = float(A), float(lam)
+        for i in range(self.d):
+            sp.kappa[i] = math.pi if kappa is None else float(kappa[i])
+            sp.theta[i] = 0.0 if theta is None else float(theta[i])
+        self._stream()
+        _abi.lhe_lbm_set_boundary_sine_product(self.h, sp)
+
     def boundary_points(self):
         """(points[P][d] as a numpy array, t_offset): the points where the Dirichlet jets of the next
         step are needed (full-way: the boundary nodes; half-way: the mid-link points of the unknown

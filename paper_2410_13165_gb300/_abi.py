@@ -31,7 +31,7 @@ EXPORTS = [
     "lhe_lbm_set_boundary_wave", "lhe_lbm_step", "lhe_lbm_macro", "lhe_lbm_diagnostics", "lhe_lbm_get_state",
     "lhe_lbm_set_state", "lhe_lbm_adjoint_seed", "lhe_lbm_adjoint_step", "lhe_lbm_adjoint_grads",
     "lhe_lbm_diagnostics_noalloc", "lhe_lbm_stability_map", "lhe_lbm_boundary_points", "lhe_lbm_set_boundary_jet",
-    "lhe_lbm_adjoint_jet_grad", "lhe_lbm_set_source",
+    "lhe_lbm_adjoint_jet_grad", "lhe_lbm_set_source", "lhe_lbm_set_boundary_sine_product",
 ]
 
 
@@ -61,6 +61,13 @@ class lhe_wave(ctypes.Structure):
         ("nmodes", ctypes.c_int32), ("reserved0", ctypes.c_int32), ("b", ctypes.c_double),
         ("g", ctypes.c_double * MAX_DIM), ("a", ctypes.c_double * MAX_MODES),
         ("kappa", ctypes.c_double * (MAX_MODES * MAX_DIM)), ("theta", ctypes.c_double * MAX_MODES),
+    ]
+
+
+class lhe_sine_product(ctypes.Structure):
+    _fields_ = [
+        ("A", ctypes.c_double), ("lam", ctypes.c_double), ("kappa", ctypes.c_double * MAX_DIM),
+        ("theta", ctypes.c_double * MAX_DIM),
     ]
 
 
@@ -100,6 +107,7 @@ def load(path: str | None = None):
         "lhe_lbm_set_source": (st, [_H, _D]),
         "lhe_lbm_init": (st, [_H, _D, _D, _D]),
         "lhe_lbm_set_boundary_wave": (st, [_H, ctypes.POINTER(lhe_wave)]),
+        "lhe_lbm_set_boundary_sine_product": (st, [_H, ctypes.POINTER(lhe_sine_product)]),
         "lhe_lbm_boundary_points": (st, [_H, _D, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double)]),
         "lhe_lbm_set_boundary_jet": (st, [_H, _D]),
         "lhe_lbm_step": (st, [_H, ctypes.c_int64]),
@@ -181,6 +189,10 @@ def lhe_lbm_init(h, phi0_ptr: int, grad_ptr: int | None, R_ptr: int | None) -> N
 
 def lhe_lbm_set_boundary_wave(h, w: lhe_wave) -> None:
     check(load().lhe_lbm_set_boundary_wave(h, ctypes.byref(w)), h)
+
+
+def lhe_lbm_set_boundary_sine_product(h, sp: lhe_sine_product) -> None:
+    check(load().lhe_lbm_set_boundary_sine_product(h, ctypes.byref(sp)), h)
 
 
 def lhe_lbm_boundary_points(h, d: int):

@@ -22,7 +22,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "liblhe_lbm.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["lhe_api.cu", "lhe_step_fp64.cu", "lhe_step_box.cu", "lhe_step_dev.cu", "lhe_step_dev_tma.cu", "lhe_boundary.cu", "lhe_misc.cu",
-           "lhe_noalloc.cu", "lhe_stability.cu"]
+           "lhe_noalloc.cu", "lhe_stability.cu", "lhe_provider.cu"]
 
 
 def _nvcc() -> str:

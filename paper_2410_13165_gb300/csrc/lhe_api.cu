@@ -439,10 +439,13 @@ lhe_status lhe_lbm_create(const lhe_lbm_params *p, lhe_lbm **out) {
     e = cudaMalloc(&l->bc_axis, sizeof(double) * 2 * (size_t)kMaxModes * (size_t)sum_n);
     if (e != cudaSuccess) return bail(cuda_fail(l, e, "cudaMalloc(boundary phase table)"));
   }
-  if (p->d == 3 && p->bc == LHE_BC_PERIODIC && p->precision == LHE_FP32_DEV && !(p->flags & LHE_FLAG_NO_STAGING)) {
-    int dev = 0, sms = 0;
+  {
+    int dev = 0;
     cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&l->sms, cudaDevAttrMultiProcessorCount, dev);
+  }
+  if (p->d == 3 && p->bc == LHE_BC_PERIODIC && p->precision == LHE_FP32_DEV && !(p->flags & LHE_FLAG_NO_STAGING)) {
+    const int sms = l->sms;
     if (sms > 0 && plan_dev3_tma(l->g, sms, l->tma)) {
       e = cudaHostAlloc((void **)&l->tma_err_host, sizeof(int32_t), cudaHostAllocMapped);
       if (e != cudaSuccess) return bail(cuda_fail(l, e, "cudaHostAlloc(pipeline flag)"));
@@ -474,6 +477,8 @@ lhe_status lhe_lbm_destroy(lhe_lbm *l) {
   cudaFree(l->bsites);
   cudaFree(l->broff);
   cudaFree(l->brec);
+  cudaFree(l->sp_R0);
+  cudaFree(l->sp_rec0);
   cudaFree(l->xface);
   cudaFree(l->bc_table);
   cudaFree(l->bc_axis);
@@ -505,6 +510,7 @@ lhe_status lhe_lbm_info(const lhe_lbm *l, lhe_lbm_info_t *info) {
 
 lhe_status lhe_lbm_set_source(lhe_lbm *l, const double *Rf) {
   if (lhe_status s = check_handle(l)) return s;
+  l->sp_mode = false;  // a caller's source ends the manufactured solution's
   if (Rf) {
     if (!l->Rnext) LHE_CK(l, cudaMalloc(&l->Rnext, sizeof(double) * (size_t)l->g.S));
     LHE_CK(l, cudaMemcpyAsync(l->Rnext, Rf, sizeof(double) * (size_t)l->g.S, cudaMemcpyDefault, l->stream));
@@ -674,6 +680,7 @@ lhe_status lhe_lbm_set_boundary_wave(lhe_lbm *l, const lhe_wave *w) {
   l->wave = *w;
   l->have_wave = true;
   l->jet_mode = false;
+  l->sp_mode = false;
   l->jet_ready = false;
   return LHE_OK;
 }
@@ -812,6 +819,84 @@ lhe_status lhe_lbm_set_boundary_jet(lhe_lbm *l, const double *jet_dev) {
   LHE_CK(l, launch_jet_records(l->p.d, l->p.bc, b, jet_dev, jet_index_table(l->p.d).data(), l->brec, l->stream));
   l->jet_mode = true;
   l->jet_ready = true;
+  l->sp_mode = false;
+  return LHE_OK;
+}
+
+lhe_status lhe_lbm_set_boundary_sine_product(lhe_lbm *l, const lhe_sine_product *sp) {
+  if (lhe_status s = check_handle(l)) return s;
+  if (l->p.bc == LHE_BC_PERIODIC) return fail(l, LHE_ERR_STATE, "boundary data on a periodic box");
+  if (!sp) return fail(l, LHE_ERR_ARG, "sine product is NULL");
+  const int d = l->p.d;
+  bool finite = std::isfinite(sp->A) && std::isfinite(sp->lambda);
+  for (int i = 0; i < d; ++i) finite = finite && std::isfinite(sp->kappa[i]) && std::isfinite(sp->theta[i]);
+  if (!finite) return fail(l, LHE_ERR_ARG, "sine product parameters must be finite");
+  if (lhe_status st = check_pipeline(l)) return st;
+  if (lhe_status st = ensure_jet_buffers(l)) return st;
+  int64_t P = 0;
+  if (lhe_status st = lhe_lbm_boundary_points(l, nullptr, &P, nullptr)) return st;
+  std::vector<double> pts((size_t)std::max<int64_t>(P, 1) * d);
+  if (lhe_status st = lhe_lbm_boundary_points(l, pts.data(), &P, nullptr)) return st;
+  // count of each variable (0: t, i: x_i) in every jet entry, in the jet order
+  std::vector<int8_t> tup;
+  for (int q = 0; q <= 3; ++q) {
+    int v[3] = {0, 0, 0};
+    for (;;) {
+      int8_t cnt[6] = {0, 0, 0, 0, 0, 0};
+      for (int j = 0; j < q; ++j) ++cnt[v[j]];
+      tup.insert(tup.end(), cnt, cnt + 6);
+      int j = q - 1;  // next non-decreasing tuple
+      while (j >= 0 && v[j] == d) --j;
+      if (j < 0) break;
+      ++v[j];
+      for (int m = j + 1; m < q; ++m) v[m] = v[j];
+    }
+  }
+  const int64_t JL = LHE_JET_LEN(d);
+  if ((int64_t)tup.size() != JL * 6) return fail(l, LHE_ERR_ARG, "jet table");
+  SineProductArgs a{};
+  a.A = sp->A;
+  a.lambda = sp->lambda;
+  for (int i = 0; i < d; ++i) {
+    a.kappa[i] = sp->kappa[i];
+    a.theta[i] = sp->theta[i];
+    a.u[i] = l->p.u[i];
+    a.x0[i] = l->x0[i];
+  }
+  a.dx = l->dx;
+  const size_t S = (size_t)l->g.S;
+  if (!l->sp_R0) LHE_CK(l, cudaMalloc(&l->sp_R0, sizeof(double) * S));
+  if (!l->sp_rec0) LHE_CK(l, cudaMalloc(&l->sp_rec0, sizeof(double) * (size_t)std::max<int64_t>(l->nrec, 1)));
+  if (!l->Rnext) LHE_CK(l, cudaMalloc(&l->Rnext, sizeof(double) * S));
+  double *dpts = nullptr, *djet = nullptr;
+  int8_t *dtup = nullptr;
+  auto release = [&]() {
+    cudaFree(dpts);
+    cudaFree(djet);
+    cudaFree(dtup);
+  };
+  cudaError_t e = cudaMalloc(&dpts, sizeof(double) * pts.size());
+  if (e == cudaSuccess) e = cudaMalloc(&djet, sizeof(double) * (size_t)std::max<int64_t>(P, 1) * JL);
+  if (e == cudaSuccess) e = cudaMalloc(&dtup, tup.size());
+  if (e == cudaSuccess) e = cudaMemcpy(dpts, pts.data(), sizeof(double) * pts.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(dtup, tup.data(), tup.size(), cudaMemcpyHostToDevice);
+  // jets of the solution at unit time factor, its source field R0, and the records they give
+  if (e == cudaSuccess) e = launch_sp_jets(d, a, dpts, P, dtup, djet, l->stream);
+  if (e == cudaSuccess) e = launch_sp_source(a, l->g, l->sp_R0, l->stream);
+  if (e == cudaSuccess) {
+    BoundaryArgs b = boundary_args(l);
+    b.roff = l->broff;
+    b.Rfield = l->sp_R0;  // data and source share the time factor in both schemes
+    e = launch_jet_records(d, l->p.bc, b, djet, jet_index_table(d).data(), l->sp_rec0, l->stream);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(l->stream);
+  release();
+  if (e != cudaSuccess) return cuda_fail(l, e, "sine-product boundary data");
+  l->sp_mode = true;
+  l->sp_lambda = sp->lambda;
+  l->jet_mode = true;
+  l->jet_ready = false;
+  l->Rnext_state = 0;
   return LHE_OK;
 }
 
@@ -840,7 +925,7 @@ lhe_status lhe_lbm_step(lhe_lbm *l, int64_t n) {
   if (!periodic && next_source(l) && !l->jet_mode && n > 0)
     return fail(l, LHE_ERR_STATE, "a per-site source on a Dirichlet box needs the boundary data as jets "
                                   "(the exact-solution family assumes a constant R)");
-  if (!periodic && l->jet_mode && n > 0) {
+  if (!periodic && l->jet_mode && !l->sp_mode && n > 0) {
     if (n != 1) return fail(l, LHE_ERR_STATE, "boundary jets hold one step's data: step n = 1 at a time");
     if (!l->jet_ready) return fail(l, LHE_ERR_STATE, "set the boundary jets of this step first (lhe_lbm_set_boundary_jet)");
   }
@@ -872,23 +957,44 @@ lhe_status lhe_lbm_step(lhe_lbm *l, int64_t n) {
         b.ph_s[m] = std::sin(ph);
       }
     }
-    // FP64 Dirichlet boxes: the row kernel also treats the x_1-face nodes of its rows
-    const bool fused = !periodic && !dev && !a.Rfield && !l->jet_mode && l->xface;
-    cudaError_t e = l->staged ? launch_step_dev3_tma(false, a, l->tma, l->stream)
-                    : fused       ? launch_step_box_fp64(d, l->p.bc, a, b, l->xface, l->g.S_rows / l->g.n[0], l->stream)
-                    : dev         ? launch_step_dev(d, false, !periodic, a, l->stream)
-                                  : launch_step_fp64(d, false, !periodic, a, l->stream);
-    if (e != cudaSuccess) return cuda_fail(l, e, "step kernel launch");
+    double rec_scale = 1.0;
+    if (l->sp_mode) {
+      // the manufactured solution: its source at t_{n+1} (this step's collision) and its records at the
+      // time of the step's data, both the unit-factor fields times exp(-lambda t)
+      if (!l->Rnext) LHE_CK(l, cudaMalloc(&l->Rnext, sizeof(double) * (size_t)l->g.S));
+      cudaError_t e0 = launch_scale_field(l->sp_R0, std::exp(-l->sp_lambda * (double)(l->step + 1) * l->dt), l->g.S, l->Rnext,
+                              l->sms, l->stream);
+      if (e0 != cudaSuccess) return cuda_fail(l, e0, "source kernel launch");
+      std::swap(l->Rfield, l->Rnext);
+      a.Rfield = l->Rfield;
+      b.Rfield = l->Rfield;
+      rec_scale = std::exp(-l->sp_lambda * (double)(l->p.bc == LHE_BC_FULLWAY ? l->step + 1 : l->step) * l->dt);
+    }
+    // boundary data of the step: the exact-solution family, or records (jets, the manufactured solution)
+    BoundaryArgs rest = b;
     if (!periodic) {
-      BoundaryArgs rest = b;
-      if (l->jet_mode) {
+      if (l->sp_mode) {
+        rest.roff = l->broff;
+        rest.rec = l->sp_rec0;
+        rest.rec_scale = rec_scale;
+      } else if (l->jet_mode) {
         rest.roff = l->broff;
         rest.rec = l->brec;
         l->jet_ready = false;
       }
-      if (fused) {
+    }
+    // FP64 Dirichlet boxes: the row kernel also treats the x_1-face nodes of its rows
+    const bool fused = !periodic && !dev && l->xface;
+    cudaError_t e = l->staged ? launch_step_dev3_tma(false, a, l->tma, l->stream)
+                    : fused       ? launch_step_box_fp64(d, l->p.bc, a, rest, l->xface, l->g.S_rows / l->g.n[0], l->stream)
+                    : dev         ? launch_step_dev(d, false, !periodic, a, l->stream)
+                                  : launch_step_fp64(d, false, !periodic, a, l->stream);
+    if (e != cudaSuccess) return cuda_fail(l, e, "step kernel launch");
+    if (!periodic) {
+      if (fused) {  // the x_1-face-only nodes lead the list and are done
         rest.sites = b.sites + l->nb_xface;
         rest.nsites = b.nsites - l->nb_xface;
+        if (rest.roff) rest.roff += l->nb_xface;
       }
       e = launch_boundary(d, l->p.bc, dev, rest, l->stream);
       if (e != cudaSuccess) return cuda_fail(l, e, "boundary kernel launch");

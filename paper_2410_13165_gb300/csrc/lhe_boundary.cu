@@ -75,7 +75,7 @@ __global__ void __launch_bounds__(128) k_boundary(const BoundaryArgs a) {
       continue;
     }
     if (jets) {
-      const double b = __ldg(rec + ju++);
+      const double b = a.rec_scale * __ldg(rec + ju++);
       v[k] = KIND == 1 ? b : b - bnode_fkb<D, DEV>(a, k, site);
     } else {
       v[k] = bnode_unknown<D, KIND, DEV>(a, nd, k, site);

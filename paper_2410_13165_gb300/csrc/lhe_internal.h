@@ -89,6 +89,14 @@ struct DevTmaPlan {
 constexpr int kCollideGeneral = 0;  // two FP64 operations per population
 constexpr int kCollideScaled = 1;   // scaled representation, one FMA per population
 
+// The manufactured solution A exp(-lambda t) prod_i sin(kappa_i x_i + theta_i) and the node grid
+// x_i = x0_i + j_i dx (lhe_provider.cu).
+struct SineProductArgs {
+  double A, lambda;
+  double kappa[kMaxD], theta[kMaxD], u[kMaxD], x0[kMaxD];
+  double dx;
+};
+
 // Arguments of the boundary-node kernels (Dirichlet boxes).
 struct BoundaryArgs {
   Geom g;
@@ -99,6 +107,7 @@ struct BoundaryArgs {
   // (half-way, Eq. (bun2) without -f*_kbar); rec == nullptr: data from the exact-solution family.
   const int32_t *roff;
   const double *rec;
+  double rec_scale = 1.0;  // factor on every record (a separable solution's time factor)
   const double *Rfield;    // per-site source R(x) of the step, or nullptr for the constant R
   const void *src;
   void *dst;
@@ -171,6 +180,10 @@ cudaError_t launch_boundary(int d, int kind, bool dev, const BoundaryArgs &a, cu
 cudaError_t launch_jet_records(int d, int kind, const BoundaryArgs &a, const double *jet, const int16_t *jidx,
                                double *rec, cudaStream_t st);
 cudaError_t launch_jet_grad(int d, int kind, const BoundaryArgs &a, const int16_t *jidx, double *out, cudaStream_t st);
+cudaError_t launch_sp_jets(int d, const SineProductArgs &a, const double *pts, int64_t P, const int8_t *tup,
+                           double *jet, cudaStream_t st);
+cudaError_t launch_sp_source(const SineProductArgs &a, const Geom &g, double *R0, cudaStream_t st);
+cudaError_t launch_scale_field(const double *in, double scale, int64_t n, double *out, int sms, cudaStream_t st);
 cudaError_t launch_step_box_fp64(int d, int kind, const StepArgs &a, const BoundaryArgs &b, double *xb, int64_t nrows,
                                  cudaStream_t st);
 cudaError_t launch_adjoint_boundary(int d, int kind, const BoundaryArgs &a, cudaStream_t st);
@@ -207,6 +220,7 @@ struct lhe_lbm {
   int32_t e[lhe::kMaxQ * lhe::kMaxD] = {};
   double x0[lhe::kMaxD] = {};
   cudaStream_t stream = nullptr;
+  int sms = 0;                  // multiprocessors of the device
   // forward state (ping-pong); FP64: double[Q*S]; FP32_DEV: float[Q*S] + phi float2[S]
   void *pop[2] = {nullptr, nullptr};
   float2 *phi[2] = {nullptr, nullptr};  // FP32_DEV: phi as a double-float pair
@@ -235,6 +249,11 @@ struct lhe_lbm {
   int64_t nrec = 0;             // records = (boundary node, unknown link) pairs
   int32_t *broff = nullptr;     // device copies, allocated by the first lhe_lbm_set_boundary_jet
   double *brec = nullptr;
+  // lhe_lbm_set_boundary_sine_product: records and source at unit time factor, scaled every step
+  bool sp_mode = false;
+  double sp_lambda = 0.0;
+  double *sp_rec0 = nullptr;
+  double *sp_R0 = nullptr;
   double *bc_table = nullptr;
   double *bc_axis = nullptr;    // per-axis phase tables of the Dirichlet data
   // adjoint

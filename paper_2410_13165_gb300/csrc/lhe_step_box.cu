@@ -14,8 +14,10 @@ constexpr int kModeGeneral = 0, kModeS2 = 1;  // collision forms, as in lhe_step
 // The unknown populations of the x_1-face nodes of a Dirichlet box (those whose other coordinates
 // are interior), for k_step_box: for interior row r (x_2..x_D interior) and side h (0: x_1 = 0, 1:
 // x_1 = n_1 - 1), the 2D - 1 unknown links (e_k,1 = +1 on the low side, -1 on the high side) at
-// xb[(2 r + h)(2D - 1) + j], exactly as the boundary-node kernel forms them: the boundary data, and
-// for the half-way scheme minus f*_kbar at the node (the state at the start of the step).
+// xb[(2 r + h)(2D - 1) + j], exactly as the boundary-node kernel forms them: the boundary data (from the
+// exact-solution family, or from the records of jets: the x_1-face-only nodes lead the boundary-node
+// list, low face then high face, each in row order), and for the half-way scheme minus f*_kbar at the
+// node (the state at the start of the step).
 template <int D, int KIND>
 __global__ void __launch_bounds__(128) k_xface_data(const BoundaryArgs b, double *__restrict__ xb, int64_t nrows) {
   constexpr Lattice<D> L{};
@@ -40,15 +42,26 @@ __global__ void __launch_bounds__(128) k_xface_data(const BoundaryArgs b, double
   int32_t site = 0;
 #pragma unroll
   for (int i = 0; i < D; ++i) site += x[i] * b.g.stride[i];
+  const int sgn = h ? -1 : 1;
+  if (b.rec) {
+    const double *rec = b.rec + b.roff[h ? nrows + (t >> 1) : (t >> 1)];
+#pragma unroll
+    for (int k = 0; k < Q; ++k)
+      if (L.e[k][0] == sgn) {
+        const int j = xface_link<D>(k, sgn);
+        const double v = b.rec_scale * __ldg(rec + j);
+        xb[t * J + j] = KIND == 1 ? v : v - bnode_fkb<D, false>(b, k, site);
+      }
+    return;
+  }
   BNode<D> nd;
   bnode_prepare<D, KIND>(b, x, nd);
-  const int sgn = h ? -1 : 1;
 #pragma unroll
   for (int k = 0; k < Q; ++k)
     if (L.e[k][0] == sgn) xb[t * J + xface_link<D>(k, sgn)] = bnode_unknown<D, KIND, false>(b, nd, k, site);
 }
 
-// Forward step of a Dirichlet box (FP64, constant R), whole x-rows through the interior: the interior
+// Forward step of a Dirichlet box (FP64; constant R or a per-site source), whole x-rows through the interior: the interior
 // lanes are those of k_step_fp64; the two face lanes of a row (x_1 = 0 or n_1 - 1, the other
 // coordinates interior) take each unknown population (e_k,1 = +1 on the low face, -1 on the high face)
 // from k_xface_data (which also subtracts the half-way scheme's f*_kbar) in the same load instruction as
@@ -82,8 +95,9 @@ __global__ void __launch_bounds__(LHE_STEP_THREADS) k_step_box(const StepArgs a,
     const int j = L.e[k][0] == 1 ? xface_link<D>(k, 1) : xface_link<D>(k, -1);
     f[k] = __ldg(unknown ? rec + j : src + k * S + source_site<D, false>(L, k, site, om, op));
   }
-  const double psi = MODE == kModeS2 ? fixed_moment_sum<Q, 1>(f) + a.dtR
-                                     : fma(a.sig, fixed_moment_sum<Q, 0>(f), a.rho_dtR);
+  const double psi = MODE == kModeS2
+                         ? fixed_moment_sum<Q, 1>(f) + (a.Rfield ? a.dt * __ldg(a.Rfield + site) : a.dtR)
+                         : fma(a.sig, fixed_moment_sum<Q, 0>(f), a.Rfield ? a.rho_dt * __ldg(a.Rfield + site) : a.rho_dtR);
 #pragma unroll
   for (int k = 0; k < Q; ++k) {
     const double out = MODE == kModeS2 ? fma(a.omega[k], psi, -f[k]) : fma(a.omega[k], psi, a.mu * f[k]);

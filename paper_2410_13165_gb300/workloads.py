@@ -231,37 +231,49 @@ def gaussian_grad(X: np.ndarray, t: float, u, A: float, xc, sigma: float) -> np.
     return -Y / (sigma * sigma) * G[None, :]
 
 
-# ---- manufactured solution with a source: phi = prod_i sin(pi x_i) exp(-t), R = phi_t + u.grad phi ----
+# ---- manufactured solution with a source: phi = A exp(-lam t) prod_i sin(kappa_i x_i + theta_i),
+#      R = phi_t + u.grad phi (defaults: A = lam = 1, kappa_i = pi, theta_i = 0) ----
 
-def sine_product_value(X: np.ndarray, t: float) -> np.ndarray:
-    return np.prod(np.sin(np.pi * X), axis=0) * math.exp(-t)
+def _sp_params(d, kappa, theta):
+    k = np.full(d, np.pi) if kappa is None else np.asarray(kappa, dtype=np.float64)[:d]
+    th = np.zeros(d) if theta is None else np.asarray(theta, dtype=np.float64)[:d]
+    return k, th
 
 
-def sine_product_grad(X: np.ndarray, t: float) -> np.ndarray:
-    s, c = np.sin(np.pi * X), np.cos(np.pi * X)
+def sine_product_value(X: np.ndarray, t: float, A=1.0, lam=1.0, kappa=None, theta=None) -> np.ndarray:
+    k, th = _sp_params(X.shape[0], kappa, theta)
+    return A * np.prod(np.sin(k[:, None] * X + th[:, None]), axis=0) * math.exp(-lam * t)
+
+
+def sine_product_grad(X: np.ndarray, t: float, A=1.0, lam=1.0, kappa=None, theta=None) -> np.ndarray:
     d = X.shape[0]
+    k, th = _sp_params(d, kappa, theta)
+    z = k[:, None] * X + th[:, None]
+    s, c = np.sin(z), np.cos(z)
     out = np.empty_like(X)
     for i in range(d):
-        out[i] = np.pi * c[i] * np.prod(np.delete(s, i, axis=0), axis=0) * math.exp(-t)
+        out[i] = A * k[i] * c[i] * np.prod(np.delete(s, i, axis=0), axis=0) * math.exp(-lam * t)
     return out
 
 
-def sine_product_source(X: np.ndarray, t: float, u) -> np.ndarray:
+def sine_product_source(X: np.ndarray, t: float, u, A=1.0, lam=1.0, kappa=None, theta=None) -> np.ndarray:
     """R(x, t) = phi_t + u.grad phi of the manufactured solution (varies in x and t)."""
-    return -sine_product_value(X, t) + np.asarray(u, dtype=np.float64) @ sine_product_grad(X, t)
+    return -lam * sine_product_value(X, t, A, lam, kappa, theta) \
+        + np.asarray(u, dtype=np.float64) @ sine_product_grad(X, t, A, lam, kappa, theta)
 
 
-def sine_product_jets(points: np.ndarray, t: float) -> np.ndarray:
-    """Jets of phi = prod_i sin(pi x_i) exp(-t): a t-derivative gives -1, an x_i-derivative one more
-    derivative of sin(pi x_i)."""
+def sine_product_jets(points: np.ndarray, t: float, A=1.0, lam=1.0, kappa=None, theta=None) -> np.ndarray:
+    """Jets of the manufactured solution at points (P, d): a t-derivative gives -lam, an x_i-derivative
+    one more derivative of sin(kappa_i x_i + theta_i) (a factor kappa_i)."""
     P, d = points.shape
+    k, th = _sp_params(d, kappa, theta)
     tuples = _jet_tuples(d)
     out = np.zeros((P, len(tuples)))
     derivs = [np.sin, np.cos, lambda z: -np.sin(z), lambda z: -np.cos(z)]
     for col, tup in enumerate(tuples):
-        val = np.full(P, math.exp(-t) * (-1.0) ** sum(1 for v in tup if v == 0))
+        val = np.full(P, A * math.exp(-lam * t) * (-lam) ** sum(1 for v in tup if v == 0))
         for i in range(d):
             q = sum(1 for v in tup if v == i + 1)
-            val = val * np.pi ** q * derivs[q % 4](np.pi * points[:, i])
+            val = val * k[i] ** q * derivs[q % 4](k[i] * points[:, i] + th[i])
         out[:, col] = val
     return out

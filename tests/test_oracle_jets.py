@@ -192,3 +192,37 @@ def test_jet_gradient_entries_by_brute_force():
                 e[0, i, j] = 1.0
                 fd = (_jet_loss(m, key, f0, jets + e, target)[0] - _jet_loss(m, key, f0, jets - e, target)[0]) / 2.0
                 assert abs(fd - G[i, j]) <= 1e-11 * (1.0 + abs(fd)), (bc, i, j, fd, G[i, j])
+
+
+def test_sine_product_inputs_are_the_solution_and_its_derivatives():
+    """The seeded manufactured-solution inputs (workloads.sine_product_*): every jet entry of order
+    1..3 against central differences of the value in (t, x), the gradient against the order-1 entries,
+    and the source against phi_t + u.grad phi from the jets (3D, general parameters)."""
+    import itertools
+
+    d, u = 3, np.array([0.1, -0.05, 0.08])
+    p = dict(A=0.8, lam=1.3, kappa=[np.pi, 2.0, 1.5], theta=[0.3, -0.2, 0.1])
+    rng = np.random.default_rng(3)
+    pts, t = rng.uniform(-1, 1, size=(6, d)), 0.37
+    J = W.sine_product_jets(pts, t, **p)
+    tuples = [tup for q in range(4) for tup in itertools.combinations_with_replacement(range(d + 1), q)]
+    h = 1e-3
+
+    def value(P, tt):
+        return W.sine_product_value(P.T, tt, **p)
+
+    def deriv(tup, P, tt):
+        if not tup:
+            return value(P, tt)
+        v, rest = tup[0], tup[1:]
+        e = np.zeros(d + 1)
+        e[v] = h
+        return (deriv(rest, P + e[1:], tt + e[0]) - deriv(rest, P - e[1:], tt - e[0])) / (2 * h)
+
+    for col, tup in enumerate(tuples):
+        ref = deriv(tup, pts, t)
+        assert np.max(np.abs(J[:, col] - ref)) < 2e-5 * max(1.0, np.max(np.abs(ref))), tup
+    G = W.sine_product_grad(pts.T, t, **p)
+    assert np.allclose(G.T, J[:, 2:2 + d], rtol=1e-14, atol=1e-15)
+    R = W.sine_product_source(pts.T, t, u, **p)
+    assert np.allclose(R, J[:, 1] + J[:, 2:2 + d] @ u, rtol=1e-13, atol=1e-14)

@@ -88,6 +88,8 @@ __global__ void __launch_bounds__(LHE_STEP_THREADS) k_step_box(const StepArgs a,
   double *__restrict__ dst = static_cast<double *>(a.dst);
   const int64_t S = a.g.S;
   const double *rec = xb + (2 * (int64_t)a.g.dv[0].div((uint32_t)t) + (face < 0 ? 1 : 0)) * J;  // face node's data
+  // a per-site source is loaded ahead of the populations, so that its latency overlaps theirs
+  const double Rs = a.Rfield ? __ldg(a.Rfield + site) : 0.0;
   double f[Q];
 #pragma unroll
   for (int k = 0; k < Q; ++k) {
@@ -95,9 +97,8 @@ __global__ void __launch_bounds__(LHE_STEP_THREADS) k_step_box(const StepArgs a,
     const int j = L.e[k][0] == 1 ? xface_link<D>(k, 1) : xface_link<D>(k, -1);
     f[k] = __ldg(unknown ? rec + j : src + k * S + source_site<D, false>(L, k, site, om, op));
   }
-  const double psi = MODE == kModeS2
-                         ? fixed_moment_sum<Q, 1>(f) + (a.Rfield ? a.dt * __ldg(a.Rfield + site) : a.dtR)
-                         : fma(a.sig, fixed_moment_sum<Q, 0>(f), a.Rfield ? a.rho_dt * __ldg(a.Rfield + site) : a.rho_dtR);
+  const double psi = MODE == kModeS2 ? fixed_moment_sum<Q, 1>(f) + (a.Rfield ? a.dt * Rs : a.dtR)
+                                     : fma(a.sig, fixed_moment_sum<Q, 0>(f), a.Rfield ? a.rho_dt * Rs : a.rho_dtR);
 #pragma unroll
   for (int k = 0; k < Q; ++k) {
     const double out = MODE == kModeS2 ? fma(a.omega[k], psi, -f[k]) : fma(a.omega[k], psi, a.mu * f[k]);

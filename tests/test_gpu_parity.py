@@ -186,6 +186,35 @@ def test_fp64_dirichlet_d4q33_12(bc, u):
     assert relerr(g, o) < FP64_TOL
 
 
+@pytest.mark.parametrize("bc,u", [("fullway", (0.05, 0.2, 0.08, 0.1)), ("halfway", (1e-3, 1e-3, 1e-3, 1e-3))])
+def test_fp64_dirichlet_d4q33_64_full_size(bc, u):
+    """Example 3's 4D box at the benchmark's size, 64^4 = 16.8 M nodes (2.0 M boundary nodes), in its
+    launch configuration (the row kernel with the x_1-face nodes, then the boundary-node kernel), 3
+    steps, every node against the oracle (about 18 GB of host memory for the oracle's buffers)."""
+    n, steps = 64, 3
+    m = O.Model(4, n, -1.0, 1.0, u, bc=bc)
+    ssum = np.pi * m.coords().sum(axis=0)
+    phi0 = np.sin(ssum)
+    grad = np.repeat((np.pi * np.cos(ssum))[None, :], 4, axis=0)
+    del ssum
+    o = m.phi(m.step(m.init(phi0, grad, 3), 0, steps, wave=m.wave(a=[1.0], kappa=[[np.pi] * 4], theta=[0.0])))
+    sim = LBM(4, n, -1.0, 1.0, u=u, bc=bc)
+    sim.init(_t(phi0), _t(grad))
+    sim.set_boundary_wave([1.0], [[np.pi] * 4], [0.0])
+    sim.step(steps)
+    g = sim.macro().cpu().numpy()
+    sim.close()
+    assert relerr(g, o) < FP64_TOL
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32dev"])
+def test_d5q51_24_full_size(precision):
+    """The precision workload's D5Q51 box at its size, 24^5 = 8.0 M nodes, u = (0.02, .., 0.1),
+    tau = 1/2, seeded modes, 3 steps, every node against the oracle."""
+    g, o = run_pair(5, 24, (0.02, 0.04, 0.06, 0.08, 0.1), 3, tau=0.5, nmodes=8, seed=5, precision=precision)
+    assert rel(g, o) < (FP64_TOL if precision == "fp64" else DEV_TOL)
+
+
 @pytest.mark.parametrize("bc", ["fullway", "halfway"])
 @pytest.mark.parametrize("d,n,u,tau", [
     (1, (23,), (0.3,), 0.5), (1, (16,), (0.1,), 0.8),

@@ -295,7 +295,7 @@ typedef struct {
  * P(x): this call forms the jets of P, the field R(x, t) exp(lambda t) and their records once
  * (synchronising the stream; P * LHE_JET_LEN(d) doubles of scratch); each step scales them by
  * exp(-lambda t). Initialise with lhe_lbm_init's R_dev = R(x, 0) so that the stored state carries the
- * solution's source. lhe_lbm_set_boundary_wave, lhe_lbm_set_boundary_jet and lhe_lbm_set_source end
+ * solution's source; lhe_lbm_set_state re-forms R(x, t_step) of the restored state. lhe_lbm_set_boundary_wave, lhe_lbm_set_boundary_jet and lhe_lbm_set_source end
  * it. Errors: LHE_ERR_STATE on a periodic box, LHE_ERR_ARG for NULL or non-finite parameters,
  * LHE_ERR_OOM / LHE_ERR_CUDA. */
 LHE_API lhe_status lhe_lbm_set_boundary_sine_product(lhe_lbm *lbm, const lhe_sine_product *sp_host);

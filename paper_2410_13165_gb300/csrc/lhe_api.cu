@@ -1069,6 +1069,12 @@ lhe_status lhe_lbm_set_state(lhe_lbm *l, const void *buf, int64_t step) {
   l->initialised = true;
   l->scale_j[0] = 0;
   l->scale_acc[0] = 0.0;
+  if (l->sp_mode) {
+    // the manufactured solution's source of the restored state's last collision, R(x, t_step)
+    if (!l->Rfield) LHE_CK(l, cudaMalloc(&l->Rfield, sizeof(double) * (size_t)l->g.S));
+    LHE_CK(l, launch_scale_field(l->sp_R0, std::exp(-l->sp_lambda * (double)step * l->dt), l->g.S, l->Rfield, l->sms,
+                                 l->stream));
+  }
   return LHE_OK;
 }
 

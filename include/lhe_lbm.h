@@ -265,7 +265,7 @@ LHE_API lhe_status lhe_lbm_set_state(lhe_lbm *lbm, const void *buf, int64_t step
  * adjoint state, each lhe_lbm_adjoint_step() applies the transpose of one step (reverse stream,
  * transposed collision) and accumulates dL/dR(x), and lhe_lbm_adjoint_grads() applies the
  * transpose of the initialisation. The adjoint uses the handle's precision and allocates its own
- * buffers on first use. Dirichlet boxes (FP64 only; LHE_ERR_STATE for FP32_DEV): the transpose of
+ * buffers on first use. Dirichlet boxes (both precisions): the transpose of
  * the boundary schemes drops the populations that leave the box (full-way, Eq. (bun1)) or returns
  * them, negated, to the opposite link of the same node (half-way, Eq. (bun2)); the boundary data
  * enter additively: lhe_lbm_adjoint_jet_grad gives their cotangent per step as jets. dL/dR(x) is not

@@ -910,7 +910,9 @@ lhe_status lhe_lbm_adjoint_jet_grad(lhe_lbm *l, double *out) {
   BoundaryArgs b = boundary_args(l);
   b.roff = l->broff;
   b.src = l->adj[l->acur];
-  LHE_CK(l, launch_jet_grad(l->p.d, l->p.bc, b, jet_index_table(l->p.d).data(), out, l->stream));
+  b.phi_src = l->adjW[l->acur];
+  LHE_CK(l, launch_jet_grad(l->p.d, l->p.bc, l->p.precision == LHE_FP32_DEV, b, jet_index_table(l->p.d).data(), out,
+                            l->stream));
   return LHE_OK;
 }
 
@@ -1081,8 +1083,6 @@ lhe_status lhe_lbm_set_state(lhe_lbm *l, const void *buf, int64_t step) {
 lhe_status lhe_lbm_adjoint_seed(lhe_lbm *l, const double *seed) {
   if (lhe_status s = check_handle(l)) return s;
   if (!seed) return fail(l, LHE_ERR_ARG, "dL/dphi_T is NULL");
-  if (l->p.bc != LHE_BC_PERIODIC && l->p.precision == LHE_FP32_DEV)
-    return fail(l, LHE_ERR_STATE, "the adjoint of a Dirichlet box is implemented for FP64 populations");
   if (!l->initialised) return fail(l, LHE_ERR_STATE, "lhe_lbm_adjoint_seed before lhe_lbm_init");
   const bool dev = l->p.precision == LHE_FP32_DEV;
   const size_t S = (size_t)l->g.S;
@@ -1129,7 +1129,9 @@ lhe_status lhe_lbm_adjoint_step(lhe_lbm *l, int64_t n) {
     if (!periodic) {
       b.src = a.src;
       b.dst = a.dst;
-      e = launch_adjoint_boundary(l->p.d, l->p.bc, b, l->stream);
+      b.phi_src = a.phi_src;
+      b.phi_dst = a.phi_dst;
+      e = launch_adjoint_boundary(l->p.d, l->p.bc, dev, b, l->stream);
       if (e != cudaSuccess) return cuda_fail(l, e, "adjoint boundary kernel launch");
     }
     l->acur ^= 1;

@@ -233,8 +233,8 @@ cudaError_t launch_jet_records(int d, int kind, const BoundaryArgs &a, const dou
 // rho_k / omega_k (the R terms and the half-way -f*_kbar do not depend on the jets). Full-way: one row
 // per boundary node, summed over its unknown links (omega_k times the cotangent is rho_k); half-way:
 // one row per unknown population, w+ and w- times rho_k / omega_k. Each thread owns the rows of its
-// node and zeroes them first.
-template <int D, int KIND>
+// node and zeroes them first. FP32 deviations (DEV): rho_k = omega_k W + eps_k.
+template <int D, int KIND, bool DEV>
 __global__ void __launch_bounds__(128) k_jet_grad(const BoundaryArgs a, const JetIndex J, double *__restrict__ out) {
   constexpr Lattice<D> L{};
   constexpr int Q = Lattice<D>::Q;
@@ -275,7 +275,8 @@ __global__ void __launch_bounds__(128) k_jet_grad(const BoundaryArgs a, const Je
     double w[D + 1];  // weights of the variables in (d_t + c.grad): 1 for t, c_i for x_i
     w[0] = 1.0;
     for (int i = 0; i < D; ++i) w[i + 1] = a.c * L.e[k][i];
-    const double rk = rho[k * S + site];
+    const double rk = DEV ? fma(a.omega[k], df_value(a.phi_src[site]), (double)static_cast<const float *>(a.src)[k * S + site])
+                          : rho[k * S + site];
     if (KIND == 1) {
       g[0] += rk;
       if (P >= 3)
@@ -314,24 +315,31 @@ __global__ void __launch_bounds__(128) k_jet_grad(const BoundaryArgs a, const Je
 }
 
 template <int D>
-static cudaError_t jet_grad_d(int kind, const BoundaryArgs &a, const JetIndex &J, double *out, cudaStream_t st) {
+static cudaError_t jet_grad_d(int kind, bool dev, const BoundaryArgs &a, const JetIndex &J, double *out,
+                              cudaStream_t st) {
   if (a.nsites <= 0) return cudaSuccess;
   const unsigned blocks = (unsigned)((a.nsites + 127) / 128);
-  if (kind == 1) k_jet_grad<D, 1><<<blocks, 128, 0, st>>>(a, J, out);
-  else k_jet_grad<D, 2><<<blocks, 128, 0, st>>>(a, J, out);
+  if (kind == 1) {
+    if (dev) k_jet_grad<D, 1, true><<<blocks, 128, 0, st>>>(a, J, out);
+    else k_jet_grad<D, 1, false><<<blocks, 128, 0, st>>>(a, J, out);
+  } else {
+    if (dev) k_jet_grad<D, 2, true><<<blocks, 128, 0, st>>>(a, J, out);
+    else k_jet_grad<D, 2, false><<<blocks, 128, 0, st>>>(a, J, out);
+  }
   return cudaGetLastError();
 }
 
-cudaError_t launch_jet_grad(int d, int kind, const BoundaryArgs &a, const int16_t *jidx, double *out, cudaStream_t st) {
+cudaError_t launch_jet_grad(int d, int kind, bool dev, const BoundaryArgs &a, const int16_t *jidx, double *out,
+                            cudaStream_t st) {
   JetIndex J;
   for (int i = 0; i < 216; ++i) J.i3[i] = jidx[i];
   for (int i = 0; i < 36; ++i) J.i2[i] = jidx[216 + i];
   switch (d) {
-    case 1: return jet_grad_d<1>(kind, a, J, out, st);
-    case 2: return jet_grad_d<2>(kind, a, J, out, st);
-    case 3: return jet_grad_d<3>(kind, a, J, out, st);
-    case 4: return jet_grad_d<4>(kind, a, J, out, st);
-    case 5: return jet_grad_d<5>(kind, a, J, out, st);
+    case 1: return jet_grad_d<1>(kind, dev, a, J, out, st);
+    case 2: return jet_grad_d<2>(kind, dev, a, J, out, st);
+    case 3: return jet_grad_d<3>(kind, dev, a, J, out, st);
+    case 4: return jet_grad_d<4>(kind, dev, a, J, out, st);
+    case 5: return jet_grad_d<5>(kind, dev, a, J, out, st);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -343,8 +351,10 @@ cudaError_t launch_jet_grad(int d, int kind, const BoundaryArgs &a, const int16_
 // the full-way scheme it feeds nothing (Eq. (bun1) sets the unknown population at the far side
 // from the boundary data alone), in the half-way scheme it is the -f*_j(x) of the unknown
 // f_jbar(x) = -f*_j(x) + B (Eq. (bun2)), so mu_j(x) = -(omega_j / omega_jbar) rho_jbar(x). Then
-// rho_k <- (1 - s) mu_k + s omega_k sum_j mu_j, as in the bulk.
-template <int D, int KIND>
+// rho_k <- (1 - s) mu_k + s omega_k sum_j mu_j, as in the bulk. FP32 deviations (DEV): the adjoint state
+// is rho_k = omega_k W + eps_k (W a double-float pair, eps in FP32), formed in FP64 here, and the result
+// is stored as the forward boundary kernel stores a state: W' = sum_j mu_j, eps'_k = rho'_k - omega_k W'.
+template <int D, int KIND, bool DEV>
 __global__ void __launch_bounds__(128) k_adj_boundary(const BoundaryArgs a) {
   constexpr Lattice<D> L{};
   constexpr int Q = Lattice<D>::Q;
@@ -367,6 +377,11 @@ __global__ void __launch_bounds__(128) k_adj_boundary(const BoundaryArgs a) {
     }
   }
   const double *__restrict__ src = static_cast<const double *>(a.src);
+  const float *__restrict__ esrc = static_cast<const float *>(a.src);
+  // the adjoint state rho_j at node o
+  auto rho = [&](int j, int32_t o) {
+    return DEV ? fma(a.omega[j], df_value(a.phi_src[o]), (double)esrc[j * S + o]) : src[j * S + o];
+  };
   double mu[Q];
 #pragma unroll
   for (int k = 0; k < Q; ++k) {
@@ -380,8 +395,20 @@ __global__ void __launch_bounds__(128) k_adj_boundary(const BoundaryArgs a) {
         o += L.e[k][i] * a.g.stride[i];
       }
     }
-    if (inside) mu[k] = src[k * S + o];
-    else mu[k] = KIND == 2 ? -a.wratio[k] * src[L.opp[k] * S + site] : 0.0;
+    if (inside) mu[k] = rho(k, o);
+    else mu[k] = KIND == 2 ? -a.wratio[k] * rho(L.opp[k], site) : 0.0;
+  }
+  if (DEV) {
+    const double M = fixed_moment_sum<Q, 0>(mu);
+    const double psi = a.s * M;
+    float *edst = static_cast<float *>(a.dst);
+#pragma unroll
+    for (int k = 0; k < Q; ++k) {
+      const double r = a.s == 2.0 ? fma(a.omega[k], psi, -mu[k]) : fma(a.omega[k], psi, a.oms * mu[k]);
+      edst[k * S + site] = (float)fma(-a.omega[k], M, r);
+    }
+    a.phi_dst[site] = df_split(M);
+    return;
   }
   double *__restrict__ dst = static_cast<double *>(a.dst);
   if (a.s == 2.0) {
@@ -396,21 +423,26 @@ __global__ void __launch_bounds__(128) k_adj_boundary(const BoundaryArgs a) {
 }
 
 template <int D>
-static cudaError_t adj_boundary_d(int kind, const BoundaryArgs &a, cudaStream_t st) {
+static cudaError_t adj_boundary_d(int kind, bool dev, const BoundaryArgs &a, cudaStream_t st) {
   if (a.nsites <= 0) return cudaSuccess;
   const unsigned blocks = (unsigned)((a.nsites + 127) / 128);
-  if (kind == 1) k_adj_boundary<D, 1><<<blocks, 128, 0, st>>>(a);
-  else k_adj_boundary<D, 2><<<blocks, 128, 0, st>>>(a);
+  if (kind == 1) {
+    if (dev) k_adj_boundary<D, 1, true><<<blocks, 128, 0, st>>>(a);
+    else k_adj_boundary<D, 1, false><<<blocks, 128, 0, st>>>(a);
+  } else {
+    if (dev) k_adj_boundary<D, 2, true><<<blocks, 128, 0, st>>>(a);
+    else k_adj_boundary<D, 2, false><<<blocks, 128, 0, st>>>(a);
+  }
   return cudaGetLastError();
 }
 
-cudaError_t launch_adjoint_boundary(int d, int kind, const BoundaryArgs &a, cudaStream_t st) {
+cudaError_t launch_adjoint_boundary(int d, int kind, bool dev, const BoundaryArgs &a, cudaStream_t st) {
   switch (d) {
-    case 1: return adj_boundary_d<1>(kind, a, st);
-    case 2: return adj_boundary_d<2>(kind, a, st);
-    case 3: return adj_boundary_d<3>(kind, a, st);
-    case 4: return adj_boundary_d<4>(kind, a, st);
-    case 5: return adj_boundary_d<5>(kind, a, st);
+    case 1: return adj_boundary_d<1>(kind, dev, a, st);
+    case 2: return adj_boundary_d<2>(kind, dev, a, st);
+    case 3: return adj_boundary_d<3>(kind, dev, a, st);
+    case 4: return adj_boundary_d<4>(kind, dev, a, st);
+    case 5: return adj_boundary_d<5>(kind, dev, a, st);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -179,14 +179,15 @@ cudaError_t launch_step_dev(int d, bool adjoint, bool interior, const StepArgs &
 cudaError_t launch_boundary(int d, int kind, bool dev, const BoundaryArgs &a, cudaStream_t st);
 cudaError_t launch_jet_records(int d, int kind, const BoundaryArgs &a, const double *jet, const int16_t *jidx,
                                double *rec, cudaStream_t st);
-cudaError_t launch_jet_grad(int d, int kind, const BoundaryArgs &a, const int16_t *jidx, double *out, cudaStream_t st);
+cudaError_t launch_jet_grad(int d, int kind, bool dev, const BoundaryArgs &a, const int16_t *jidx, double *out,
+                            cudaStream_t st);
 cudaError_t launch_sp_jets(int d, const SineProductArgs &a, const double *pts, int64_t P, const int8_t *tup,
                            double *jet, cudaStream_t st);
 cudaError_t launch_sp_source(const SineProductArgs &a, const Geom &g, double *R0, cudaStream_t st);
 cudaError_t launch_scale_field(const double *in, double scale, int64_t n, double *out, int sms, cudaStream_t st);
 cudaError_t launch_step_box_fp64(int d, int kind, const StepArgs &a, const BoundaryArgs &b, double *xb, int64_t nrows,
                                  cudaStream_t st);
-cudaError_t launch_adjoint_boundary(int d, int kind, const BoundaryArgs &a, cudaStream_t st);
+cudaError_t launch_adjoint_boundary(int d, int kind, bool dev, const BoundaryArgs &a, cudaStream_t st);
 cudaError_t launch_stability(int d, const double *omega_dev, int64_t npoints, int32_t nxi, double s,
                              unsigned long long *rho_bits_dev, cudaStream_t st);
 cudaError_t launch_init(int d, bool dev, const InitArgs &a, cudaStream_t st);

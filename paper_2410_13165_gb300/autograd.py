@@ -36,7 +36,7 @@ class LBMFunction(torch.autograd.Function):
 
 
 class LBMBoxFunction(torch.autograd.Function):
-    """phi(T) = F(phi0, grad phi0, jets) for a Dirichlet box (FP64 handle) whose boundary data are given
+    """phi(T) = F(phi0, grad phi0, jets) for a Dirichlet box (either precision) whose boundary data are given
     as jets, one (P, jet_len(d)) block per step at sim.boundary_points() (jets: (T, P, jet_len(d))).
     Gradients w.r.t. all three: the adjoint steps run from the cotangent of phi(T), the cotangent of
     each step's jets is read before its adjoint step (Eq. (bun1) / Eq. (bun2) transposed), and the

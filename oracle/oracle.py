@@ -68,38 +68,60 @@ _D = ctypes.POINTER(ctypes.c_double)
 _I = ctypes.POINTER(ctypes.c_int)
 
 
+def load(path: str) -> ctypes.CDLL:
+    """Load an oracle library built from lhe_oracle.c (the default build, or a copy with a planted
+    mistake that a test compiles to show that a pin catches it) and declare its signatures."""
+    L = ctypes.CDLL(path)
+    L.orc_velocities.argtypes = [ctypes.c_int, _I]
+    L.orc_moment_matrix.argtypes = [ctypes.c_int, _I, _D]
+    L.orc_eps.argtypes = [ctypes.c_int, _D, _D, _D]
+    L.orc_m4_rule.argtypes = [ctypes.c_int, _D, ctypes.c_double]
+    L.orc_m4_rule.restype = ctypes.c_double
+    L.orc_weights_closed.argtypes = [ctypes.c_int, _D, _D, _D]
+    L.orc_solve.argtypes = [ctypes.c_int, _D, _D]
+    L.orc_set_threads.argtypes = [ctypes.c_int]
+    P = ctypes.POINTER(OrcModel)
+    W = ctypes.POINTER(OrcWave)
+    L.orc_init.argtypes = [P, ctypes.c_int, _D, _D, _D]
+    L.orc_fd_grad.argtypes = [P, _D, _D]
+    L.orc_step.argtypes = [P, W, ctypes.c_int64, _D, _D, _D, _D]
+    L.orc_phi.argtypes = [P, _D, _D]
+    L.orc_exact.argtypes = [P, W, _D, ctypes.c_double]
+    L.orc_exact.restype = ctypes.c_double
+    L.orc_dir_deriv.argtypes = [P, W, _D, ctypes.c_double, _D, ctypes.c_int, ctypes.c_int]
+    L.orc_dir_deriv.restype = ctypes.c_double
+    L.orc_node_coord.argtypes = [P, ctypes.c_int64, _D]
+    L.orc_exact_field.argtypes = [P, W, ctypes.c_double, _D]
+    L.orc_exact_grad_field.argtypes = [P, W, ctypes.c_double, _D]
+    L.orc_entropy.argtypes = [P, _D]
+    L.orc_entropy.restype = ctypes.c_double
+    L.orc_adjoint_step.argtypes = [P, _D, _D, _D]
+    L.orc_adjoint_init.argtypes = [P, ctypes.c_int, ctypes.c_int, _D, _D, _D]
+    return L
+
+
+def build_variant(source: str, out_path: str) -> str:
+    """Compile C source text (lhe_oracle.c with a planted mistake) with the oracle's own flags."""
+    src = out_path + ".c"
+    with open(src, "w") as fh:
+        fh.write(source)
+    cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-fopenmp",
+           "-std=c11", "-I", _HERE, "-o", out_path, src, "-lm"]
+    subprocess.run(cmd, check=True)
+    return out_path
+
+
+def source() -> str:
+    with open(_SRC) as fh:
+        return fh.read()
+
+
 def lib():
     global _lib
     with _lock:
         if _lib is None:
             build()
-            L = ctypes.CDLL(_LIBPATH)
-            L.orc_velocities.argtypes = [ctypes.c_int, _I]
-            L.orc_moment_matrix.argtypes = [ctypes.c_int, _I, _D]
-            L.orc_eps.argtypes = [ctypes.c_int, _D, _D, _D]
-            L.orc_m4_rule.argtypes = [ctypes.c_int, _D, ctypes.c_double]
-            L.orc_m4_rule.restype = ctypes.c_double
-            L.orc_weights_closed.argtypes = [ctypes.c_int, _D, _D, _D]
-            L.orc_solve.argtypes = [ctypes.c_int, _D, _D]
-            L.orc_set_threads.argtypes = [ctypes.c_int]
-            P = ctypes.POINTER(OrcModel)
-            W = ctypes.POINTER(OrcWave)
-            L.orc_init.argtypes = [P, ctypes.c_int, _D, _D, _D]
-            L.orc_fd_grad.argtypes = [P, _D, _D]
-            L.orc_step.argtypes = [P, W, ctypes.c_int64, _D, _D, _D, _D]
-            L.orc_phi.argtypes = [P, _D, _D]
-            L.orc_exact.argtypes = [P, W, _D, ctypes.c_double]
-            L.orc_exact.restype = ctypes.c_double
-            L.orc_dir_deriv.argtypes = [P, W, _D, ctypes.c_double, _D, ctypes.c_int, ctypes.c_int]
-            L.orc_dir_deriv.restype = ctypes.c_double
-            L.orc_node_coord.argtypes = [P, ctypes.c_int64, _D]
-            L.orc_exact_field.argtypes = [P, W, ctypes.c_double, _D]
-            L.orc_exact_grad_field.argtypes = [P, W, ctypes.c_double, _D]
-            L.orc_entropy.argtypes = [P, _D]
-            L.orc_entropy.restype = ctypes.c_double
-            L.orc_adjoint_step.argtypes = [P, _D, _D, _D]
-            L.orc_adjoint_init.argtypes = [P, ctypes.c_int, ctypes.c_int, _D, _D, _D]
-            _lib = L
+            _lib = load(_LIBPATH)
     return _lib
 
 

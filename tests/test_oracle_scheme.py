@@ -263,3 +263,118 @@ def test_entropy_region_equals_l2_region(d):
     away = np.abs(omin) > 1e-12
     assert np.count_nonzero(away & (omin < 0)) > 5 and np.count_nonzero(away & (omin > 0)) > 5
     assert np.all((omin[away] > 0) == (rho[away] <= 1.0 + 1e-9))
+
+
+# ----------------------------------------------------------------- finite-difference gradient and source field
+
+def _lattice_X(m):
+    return np.round((m.coords() - m.x0[:, None]) / m.dx).astype(np.int64)   # integer coordinates (d, S)
+
+
+def _fd_symbol_error(m, rng, nmodes=3):
+    """Apply the oracle's finite-difference gradient to single lattice Fourier modes cos(xi.X + theta)
+    (xi_i = 2 pi m_i / n_i) and compare with the closed form of the periodic fourth-order central
+    difference: on e^{i xi.X} it multiplies by i (8 sin xi_i - sin 2 xi_i) / (6 dx), so component i of
+    the gradient of cos(xi.X + theta) is -(8 sin xi_i - sin 2 xi_i) / (6 dx) sin(xi.X + theta).
+    Returns the largest error relative to the largest exact value."""
+    X = _lattice_X(m)
+    worst = 0.0
+    for _ in range(nmodes):
+        xi = 2 * np.pi * np.array([rng.integers(1, n) for n in m.n]) / np.asarray(m.n)
+        th = rng.uniform(0, 2 * np.pi)
+        ph = xi @ X + th
+        got = m.fd_grad(np.cos(ph))
+        sym = (8 * np.sin(xi) - np.sin(2 * xi)) / (6 * m.dx)
+        want = -sym[:, None] * np.sin(ph)[None, :]
+        worst = max(worst, float(np.max(np.abs(got - want)) / np.max(np.abs(want))))
+    return worst
+
+
+def _source_error(m, rng):
+    """One step from f = 0 with a per-site source R(x) = cos(xi.X + theta): the collision gives
+    f*_k(x) = dt omega_k R(x) (Eq. (BGK-LB-Evolution) with the source term R_k = omega_k R of Eq. (0-1-meq)'s
+    m^R = eps R, taken at the collision site), and streaming moves it to x + e_k, so the pre-collision
+    populations after the step are f_k(x) = dt omega_k R(x - e_k). Returns the largest error relative
+    to dt max omega_k."""
+    X = _lattice_X(m)
+    xi = 2 * np.pi * np.array([rng.integers(1, n) for n in m.n]) / np.asarray(m.n)
+    th = rng.uniform(0, 2 * np.pi)
+    R = np.cos(xi @ X + th)
+    got = m.step(np.zeros((m.Q, m.S)), 0, 1, Rfield=np.ascontiguousarray(R))
+    src = np.mod(X[None, :, :] - m.e[:, :, None], np.asarray(m.n)[None, :, None])   # (Q, d, S), periodic wrap
+    stride = np.cumprod([1] + list(m.n[:-1]))                                          # x_1 fastest
+    want = m.dt * m.omega[:, None] * R[np.einsum("kis,i->ks", src, stride)]
+    return float(np.max(np.abs(got - want)) / (m.dt * np.max(np.abs(m.omega))))  # 0 up to rounding
+
+
+def _ragged_model(d, tau=0.5):
+    n = [7, 9, 11, 6, 5][:d]
+    h = 0.05
+    return O.Model(d, n, 0.0, h * np.asarray(n, dtype=float), (0.1, -0.05, 0.08, 0.02, -0.03)[:d], tau=tau)
+
+
+@pytest.mark.parametrize("d", [1, 2, 3, 5])
+def test_fd_gradient_is_the_fourth_order_central_difference_symbol(d):
+    assert _fd_symbol_error(_ragged_model(d), np.random.default_rng(40 + d)) < 1e-13
+
+
+def test_third_order_init_with_the_fd_gradient_converges_at_fourth_order():
+    """Table 2 pattern with no gradient passed: the initialisation of Eq. (ini-simp) takes the
+    finite-difference gradient, whose O(dx^4) error enters f only as (dt/2) O(dx^4)."""
+    def err(N):
+        m = O.Model(2, N, 0.0, 1.0, (0.1, 0.2))
+        w = _fourier_wave(m, np.random.default_rng(11))
+        f = m.init(m.exact(w, 0.0), None, order=3)
+        n = int(round(0.5 / m.dt))
+        return O.rmse(m.phi(m.step(f, 0, n)), m.exact(w, n * m.dt))
+    sl = _slopes([err(N) for N in (16, 32, 64)])
+    assert all(3.6 < s < 4.6 for s in sl), sl
+
+
+@pytest.mark.parametrize("d,tau", [(1, 0.5), (2, 0.5), (2, 0.8), (3, 1.2), (4, 0.6)])
+def test_source_field_enters_at_the_collision_site(d, tau):
+    assert _source_error(_ragged_model(d, tau), np.random.default_rng(50 + d)) < 1e-14
+
+
+# Planted mistakes: each is a plausible slip in lhe_oracle.c that an earlier pin set would not see
+# (mass and entropy are blind to the gradient's stencil, and a constant source cannot tell where R(x)
+# is read); the pins above must reject every one. The variant is compiled from the oracle's own source
+# with one edit, on the CPU, and swapped in for the duration of the check.
+_FD_LINE = "grad[(int64_t)i * S + site] = (-v[4] + 8.0 * v[3] - 8.0 * v[1] + v[0]) / (12.0 * m->dx);"
+_PUSH_LINE = "if (inside) fnew[(int64_t)k * S + idx_to_site(m, dst)] = fstar[(int64_t)k * S + site];"
+_SRC_LINE = "fstar[(int64_t)k * S + site] = fk - m->s * (fk - feq) + m->dt * m->omega[k] * R;"
+_MUTANTS = {
+    "fd stencil sign": (_FD_LINE, _FD_LINE.replace("(-v[4] + 8.0 * v[3] - 8.0 * v[1] + v[0])",
+                                                   "(v[4] - 8.0 * v[3] + 8.0 * v[1] - v[0])")),
+    "fd dropped term": (_FD_LINE, _FD_LINE.replace(" + v[0])", ")")),
+    "fd second-order stencil": (_FD_LINE, _FD_LINE.replace("(-v[4] + 8.0 * v[3] - 8.0 * v[1] + v[0]) / (12.0 * m->dx)",
+                                                           "(v[3] - v[1]) / (2.0 * m->dx)")),
+    "fd neighbours along the wrong axis": (
+        "nb[i] = ((idx[i] + o) % m->n[i] + m->n[i]) % m->n[i];\n        v[o + 2] = phi[",
+        "nb[(i + 1) % m->d] = ((idx[(i + 1) % m->d] + o) % m->n[(i + 1) % m->d] + m->n[(i + 1) % m->d]) % "
+        "m->n[(i + 1) % m->d];\n        v[o + 2] = phi["),
+    "source read at the push destination": (
+        _PUSH_LINE,
+        "if (inside) { const int64_t ds = idx_to_site(m, dst); fnew[(int64_t)k * S + ds] = fstar[(int64_t)k * S + site]"
+        " + (Rfield ? m->dt * m->omega[k] * (Rfield[ds] - Rfield[site]) : 0.0); }"),
+    "source without the weight omega_k": (_SRC_LINE, _SRC_LINE.replace("m->dt * m->omega[k] * R", "m->dt * R / m->Q")),
+}
+
+
+@pytest.mark.parametrize("name", sorted(_MUTANTS))
+def test_the_pins_reject_planted_mistakes(name, tmp_path, monkeypatch):
+    old, new = _MUTANTS[name]
+    src = O.source()
+    assert src.count(old) == 1, "the line to mutate is not unique in lhe_oracle.c"
+    lib = O.load(O.build_variant(src.replace(old, new), str(tmp_path / "liblhe_oracle_variant.so")))
+    with monkeypatch.context() as mp:
+        mp.setattr(O, "_lib", lib)
+        fd = max(_fd_symbol_error(_ragged_model(d), np.random.default_rng(40 + d)) for d in (2, 3))
+        src_err = max(_source_error(_ragged_model(d, tau), np.random.default_rng(50 + d)) for d, tau in ((2, 0.5), (3, 1.2)))
+    if name.startswith("fd"):
+        assert fd > 1e-3, (name, fd)
+    else:
+        assert src_err > 1e-3, (name, src_err)
+    # the unmutated oracle passes both
+    assert _fd_symbol_error(_ragged_model(2), np.random.default_rng(42)) < 1e-13
+    assert _source_error(_ragged_model(2), np.random.default_rng(52)) < 1e-14

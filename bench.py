@@ -86,19 +86,23 @@ def profiled_traffic(kernel_src: str):
 
 
 class ClockSampler:
-    """nvidia-smi samples of SM clock and throttle reasons while the timed region runs."""
+    """nvidia-smi samples of SM clock and throttle reasons, each with nvidia-smi's own timestamp, taken
+    every `interval_ms` for as long as the sampler runs; summary(t0, t1) keeps the samples inside a
+    timed region (wall-clock datetimes of its start and end)."""
 
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    REASONS = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
 
-    def __init__(self, gpu_index: int):
-        self.gpu, self.lines, self.proc = gpu_index, [], None
+    def __init__(self, gpu_index: int, interval_ms: int = 20):
+        self.gpu, self.interval, self.samples, self.proc = gpu_index, interval_ms, [], None
+        self.windows = []
 
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
-                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                          "--format=csv,noheader,nounits", "-lms", str(self.interval)],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -107,8 +111,19 @@ class ClockSampler:
         return self
 
     def _read(self):
+        import datetime
+
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 10:
+                continue
+            try:
+                ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f")
+                sm, mx = float(parts[2]), float(parts[3])
+            except ValueError:
+                continue
+            reasons = {nm for nm, v in zip(self.REASONS, parts[6:10]) if v.lower() == "active"}
+            self.samples.append((ts, sm, mx, reasons))
 
     def __exit__(self, *exc):
         if self.proc:
@@ -119,23 +134,50 @@ class ClockSampler:
                 self.proc.kill()
             self.t.join(timeout=2)
 
-    def summary(self):
-        sm, mx, reasons = [], None, set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
-            parts = [p.strip() for p in ln.split(",")]
-            if len(parts) < 9:
-                continue
+    @staticmethod
+    def now():
+        import datetime
+
+        return datetime.datetime.now()
+
+    def mark(self):
+        """Context manager recording a timed region's window (see summary_windows)."""
+        import contextlib
+
+        @contextlib.contextmanager
+        def cm():
+            t0 = self.now()
             try:
-                sm.append(float(parts[1]))
-                mx = float(parts[2])
-            except ValueError:
-                continue
-            for nm, v in zip(names, parts[5:9]):
-                if v.lower() == "active":
-                    reasons.add(nm)
-        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
-                "samples": len(sm)}
+                yield
+            finally:
+                self.windows.append((t0, self.now()))
+        return cm()
+
+    def summary_windows(self, windows=None):
+        """Clocks over the samples that fall inside any of the windows (default: every window marked)."""
+        ws = list(self.windows if windows is None else windows)
+        sel = [x for x in list(self.samples) if any(a <= x[0] <= b for a, b in ws)]
+        reasons = set()
+        for x in sel:
+            reasons |= x[3]
+        return {"sm_mhz": float(np.median([x[1] for x in sel])) if sel else None,
+                "sm_max_mhz": sel[-1][2] if sel else None, "reasons": sorted(reasons), "samples": len(sel),
+                "interval_ms": self.interval, "windows": len(ws),
+                "window_s": float(sum((b - a).total_seconds() for a, b in ws))}
+
+    def summary(self, t0=None, t1=None):
+        """Median SM clock, max clock, every throttle reason seen and the sample count in [t0, t1]
+        (all samples when no window is given)."""
+        sel = [x for x in list(self.samples) if (t0 is None or x[0] >= t0) and (t1 is None or x[0] <= t1)]
+        reasons = set()
+        for x in sel:
+            reasons |= x[3]
+        out = {"sm_mhz": float(np.median([x[1] for x in sel])) if sel else None,
+               "sm_max_mhz": sel[-1][2] if sel else None, "reasons": sorted(reasons), "samples": len(sel),
+               "interval_ms": self.interval}
+        if t0 is not None and t1 is not None:
+            out["window_s"] = (t1 - t0).total_seconds()
+        return out
 
 
 def dist_setup():
@@ -233,6 +275,11 @@ def run_reference(args):
 
 
 def run_ours(args):
+    with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
+        return _run_ours(args, clk)
+
+
+def _run_ours(args, clk):
     import torch
 
     from paper_2410_13165_gb300 import LBM, build
@@ -279,7 +326,7 @@ def run_ours(args):
     nev = len(order) + 2
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(nev)] for _ in range(K)]
     barrier(ws)
-    with ClockSampler(local) as clk:
+    with clk.mark():
         t_start = torch.cuda.Event(enable_timing=True)
         t_end = torch.cuda.Event(enable_timing=True)
         t_start.record(stream)
@@ -287,6 +334,7 @@ def run_ours(args):
             one_pass(evs[k])
         t_end.record(stream)
         barrier(ws)
+    timed_window = clk.windows[-1]
     total_ms = t_start.elapsed_time(t_end)
     names = order + ["adjoint"]
     per = {name: 0.0 for name in names}
@@ -308,12 +356,17 @@ def run_ours(args):
     # the s = 2 collision (tau = 1/2) outside the timed pass, for reference
     half = LBM(3, n, u=U, tau=0.5)
     half.init(phi0, grad)
-    ms_half = barrier_max(_timed(lambda: half.step(1), 50), ws)
+    ms_half = barrier_max(_timed(lambda: half.step(1), 50, clk=clk), ws)
     half.close()
     gbs = BYTES_PER_SITE["fp64"] * S / (ms_half * 1e-3) / 1e9
     forms["fp64_tau0.5"] = {"mlups": whole_job_mlups(S, ws, ms_half), "ms_per_lb_step": ms_half, "gbs_per_gpu": gbs,
                             "frac_of_hbm": gbs / peak, "bytes_per_site": BYTES_PER_SITE["fp64"],
                             "note": "s = 2 collision, timed separately (50 steps)"}
+    # the precision form at 128^3 (the precision workload's grid), where a step is ~0.1 ms and fixed
+    # costs per launch weigh most: FP32 deviations vs FP64 in calls of one step and of 50 steps
+    forms["precision_128"] = precision_ratio_128(W, LBM, clk, ws)
+    # the differentiation workload (D3Q19 128^3, FP32 deviations, T = 1024 through torch.autograd)
+    forms["differentiation_128"] = differentiation_workload(clk)
     fp64 = forms["fp64"]
     kernel_src = os.path.join(ROOT, "paper_2410_13165_gb300", "csrc", "lhe_step_fp64.cu")
     traffic = profiled_traffic(kernel_src)
@@ -368,7 +421,8 @@ def run_ours(args):
                              "frac": fp64["gbs_per_gpu"] / peak, "traffic": traffic,
                              "algorithmic_bytes_per_launch": BYTES_PER_SITE["fp64"] * S},
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": (len(order) + 1) * K,
-                "clocks": clk.summary()}
+                "clocks": clk.summary(*timed_window),
+                "clocks_all_timed_regions": clk.summary_windows()}
         print(json.dumps(line))
     if ws > 1:
         import torch.distributed as dist
@@ -377,25 +431,100 @@ def run_ours(args):
     return 0
 
 
+def precision_ratio_128(W, LBM, clk, ws, n=128):
+    """FP32-deviation vs FP64 step time on D3Q19 n^3 (periodic, the workload's modes and u) at tau = 1/2
+    (the precision workload) and 0.8, in calls of one step and of 50 steps."""
+    import torch
+
+    phi0_np, grad_np, _, _ = W.periodic_problem(3, n, NMODES, SEED)
+    phi0 = torch.from_numpy(phi0_np).cuda()
+    grad = torch.from_numpy(np.ascontiguousarray(grad_np).ravel()).cuda()
+    peak, _ = measured_peaks()
+    out = {"n": n}
+    for tau in (0.5, TAU_DEV):
+        ms = {}
+        for prec in ("fp64", "fp32dev"):
+            sim = LBM(3, n, u=U, tau=tau, precision=prec)
+            sim.init(phi0, grad)
+            one = barrier_max(_timed(lambda: sim.step(1), 200, clk=clk), ws)
+            many = barrier_max(_timed(lambda: sim.step(50), 4, clk=clk), ws) / 50
+            sim.close()
+            bps = BYTES_PER_SITE[prec]
+            ms[prec] = {"ms_one_step_calls": one, "ms_50_step_calls": many,
+                        "frac_of_hbm_one_step_calls": bps * n ** 3 / (one * 1e-3) / 1e9 / peak,
+                        "frac_of_hbm_50_step_calls": bps * n ** 3 / (many * 1e-3) / 1e9 / peak}
+        out["tau%g" % tau] = dict(ms, ratio_one_step_calls=ms["fp64"]["ms_one_step_calls"] / ms["fp32dev"]["ms_one_step_calls"],
+                                  ratio_50_step_calls=ms["fp64"]["ms_50_step_calls"] / ms["fp32dev"]["ms_50_step_calls"])
+    return out
+
+
+def differentiation_workload(clk, n=128, T=1024, reps=3):
+    """D3Q19 n^3, FP32-deviation forward of T steps, loss 1/2 |phi(T) - target|^2, gradients w.r.t.
+    phi0 and R(x) through torch.autograd (the backward pass is T adjoint steps: the scheme is affine
+    in the state, so nothing is recomputed). Returns forward / backward times and their ratio."""
+    import torch
+
+    from paper_2410_13165_gb300 import LBM
+    from paper_2410_13165_gb300 import workloads as W
+    from paper_2410_13165_gb300.autograd import lbm_loss
+
+    X = W.node_coords(3, n, 0.0, 1.0 / n)
+    phi0 = torch.from_numpy(W.fourier_field(3, NMODES, SEED).value(X)).cuda()
+    R = torch.from_numpy(0.1 * W.fourier_field(3, 4, SEED + 10).value(X)).cuda()
+    target = torch.from_numpy(W.fourier_field(3, 8, SEED + 11).value(X)).cuda()
+    del X
+    sim = LBM(3, n, u=U, precision="fp32dev")
+    times = {"forward": [], "backward": []}
+    for rep in range(reps + 1):
+        p, r = phi0.clone().requires_grad_(True), R.clone().requires_grad_(True)
+        torch.cuda.synchronize()
+        a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        with (clk.mark() if rep else _null()):
+            a.record()
+            loss = lbm_loss(p, r, sim, T, target)
+            b.record()
+            loss.backward()
+            c.record()
+            torch.cuda.synchronize()
+        if rep:
+            times["forward"].append(a.elapsed_time(b))
+            times["backward"].append(b.elapsed_time(c))
+    sim.close()
+    fw, bw = float(np.mean(times["forward"])), float(np.mean(times["backward"]))
+    return {"T": T, "forward_ms": fw, "backward_ms": bw, "backward_over_forward": bw / fw, "loss": float(loss),
+            "note": "no recomputation: the backward pass is T adjoint steps from dL/dphi_T"}
+
+
+def _null():
+    import contextlib
+
+    return contextlib.nullcontext()
+
+
 # ------------------------------------------------------------------------------------------------
 # Other workloads of the same path (each prints one JSON line; the default is the line above).
 
-def _timed(fn, steps, warmup=3):
+def _timed(fn, steps, warmup=3, clk=None):
+    """Mean milliseconds per call of fn over `steps` calls after `warmup` calls (CUDA events on the
+    current stream); the timed region's window is recorded on the clock sampler when one is given."""
+    import contextlib
+
     import torch
 
     for _ in range(warmup):
         fn()
     torch.cuda.synchronize()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a.record()
-    for _ in range(steps):
-        fn()
-    b.record()
-    torch.cuda.synchronize()
+    with (clk.mark() if clk is not None else contextlib.nullcontext()):
+        a.record()
+        for _ in range(steps):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
     return a.elapsed_time(b) / steps
 
 
-def run_d4q33_dirichlet(args):
+def run_d4q33_dirichlet(args, clk):
     """Example 3's 4D box [-1, 1]^4 (64^4 nodes), phi = sin(pi sum_i (x_i - u_i t)): full-way at
     u = (0.05, 0.2, 0.08, 0.1) and half-way at u = 1e-3 (1,1,1,1), order-4 boundaries, K = 3 init; then
     the same boxes with the manufactured solution exp(-t) prod_i sin(pi x_i) and its source."""
@@ -416,7 +545,7 @@ def run_d4q33_dirichlet(args):
         sim = LBM(4, n, -1.0, 1.0, u=u, bc=bc)
         sim.init(phi0, grad)
         sim.set_boundary_wave([1.0], [[np.pi] * 4], [0.0])
-        ms = _timed(lambda: sim.step(1), args.steps)
+        ms = _timed(lambda: sim.step(1), args.steps, clk=clk)
         T = sim.step_index * sim.dt
         exact = np.sin(np.pi * (X - np.asarray(u)[:, None] * T).sum(axis=0))
         err = float(np.sqrt(np.mean((sim.macro().cpu().numpy() - exact) ** 2)))
@@ -436,7 +565,7 @@ def run_d4q33_dirichlet(args):
                  torch.from_numpy(W.sine_product_grad(X, 0.0).ravel()).cuda(),
                  torch.from_numpy(W.sine_product_source(X, 0.0, u)).cuda())
         sim.set_boundary_sine_product()
-        ms = _timed(lambda: sim.step(1), args.steps)
+        ms = _timed(lambda: sim.step(1), args.steps, clk=clk)
         T = sim.step_index * sim.dt
         exact = W.sine_product_value(X, T)
         err = float(np.sqrt(np.mean((sim.macro().cpu().numpy() - exact) ** 2)))
@@ -445,87 +574,84 @@ def run_d4q33_dirichlet(args):
                                      "data": "exp(-t) prod_i sin(pi x_i), source phi_t + u.grad phi, device-formed"}
         sim.close()
         del X, exact
+    out["clocks"] = clk.summary_windows()
+    out.setdefault("clocks", clk.summary())
     print(json.dumps(out))
     return 0
 
 
-def run_d5q51_fp32dev(args):
-    """D5Q51 24^5 periodic (7.96 M nodes): FP32-deviation vs FP64 MLUPS, and the FP32-deviation
-    error against the FP64 path (which matches the oracle to 1e-13) after 2000 steps."""
+def run_d5q51_fp32dev(args, clk):
+    """D5Q51 24^5 periodic (7.96 M nodes), tau = 1/2: FP32-deviation vs FP64 MLUPS, and the error of
+    both against the FP64 CPU oracle: on the 24^5 box after --oracle-steps steps (the oracle's run
+    time bounds that count) and on a 12^5 box after --error-steps steps (the workload's 2000)."""
     import torch
 
+    from oracle import oracle as O
     from paper_2410_13165_gb300 import LBM, build
     from paper_2410_13165_gb300 import workloads as W
 
     build.build()
+    O.set_threads(os.cpu_count() or 1)
     n = args.n if args.n != 256 else 24
-    T = args.error_steps
     u = (0.02, 0.04, 0.06, 0.08, 0.1)
-    X = W.node_coords(5, n, 0.0, 1.0 / n)
-    F = W.fourier_field(5, NMODES, SEED + 3)
-    phi0 = torch.from_numpy(F.value(X)).cuda()
-    grad = torch.from_numpy(np.ascontiguousarray(F.grad(X)).ravel()).cuda()
-    res, phis = {}, {}
+
+    def problem(nn):
+        X = W.node_coords(5, nn, 0.0, 1.0 / nn)
+        F = W.fourier_field(5, NMODES, SEED + 3)
+        return F.value(X), np.ascontiguousarray(F.grad(X))
+
+    phi0_np, grad_np = problem(n)
+    phi0 = torch.from_numpy(phi0_np).cuda()
+    grad = torch.from_numpy(grad_np.ravel()).cuda()
+    res = {}
     for prec, bps in (("fp64", 816), ("fp32dev", 424)):
         sim = LBM(5, n, u=u, precision=prec)
         sim.init(phi0, grad)
-        ms = _timed(lambda: sim.step(1), args.steps)
-        if T > 0:
-            sim.init(phi0, grad)
-            sim.step(T)
-            phis[prec] = sim.macro().cpu().numpy()
+        ms = _timed(lambda: sim.step(1), args.steps, clk=clk)
         res[prec] = {"mlups": n ** 5 / (ms * 1e-3) / 1e6, "ms_per_step": ms,
                      "gbs": bps * n ** 5 / (ms * 1e-3) / 1e9, "bytes_per_site": bps}
         sim.close()
     peak, _ = measured_peaks()
     for v in res.values():
         v["frac_of_hbm"] = v["gbs"] / peak
-    err = float(np.max(np.abs(phis["fp32dev"] - phis["fp64"])) / np.max(np.abs(phis["fp64"]))) if T > 0 else None
+
+    def errors(nn, steps, phi0_np, grad_np):
+        m = O.Model(5, nn, 0.0, 1.0, u)
+        t0 = time.perf_counter()
+        ref = m.phi(m.step(m.init(phi0_np, grad_np, 3), 0, steps))
+        secs = time.perf_counter() - t0
+        out = {"grid": "%d^5" % nn, "steps": steps, "oracle_seconds": secs}
+        for prec in ("fp64", "fp32dev"):
+            sim = LBM(5, nn, u=u, precision=prec)
+            sim.init(torch.from_numpy(phi0_np).cuda(), torch.from_numpy(grad_np.ravel()).cuda())
+            sim.step(steps)
+            out["rel_maxnorm_err_%s_vs_oracle" % prec] = float(
+                np.max(np.abs(sim.macro().cpu().numpy() - ref)) / np.max(np.abs(ref)))
+            sim.close()
+        return out
+
+    errs = [errors(n, args.oracle_steps, phi0_np, grad_np)]
+    if args.error_steps > 0:
+        errs.append(errors(12, args.error_steps, *problem(12)))
     print(json.dumps({"metric": "MLUPS, D5Q51 %d^5 periodic: FP64 vs FP32-deviation" % n, "unit": UNIT,
                       "forms": res, "ratio_fp32dev_over_fp64": res["fp32dev"]["mlups"] / res["fp64"]["mlups"],
-                      "rel_maxnorm_err_fp32dev_vs_fp64_after_%d_steps" % T: err}))
+                      "errors_vs_oracle": errs, "clocks": clk.summary_windows()}))
     return 0
 
 
-def run_adjoint_ratio(args):
+def run_adjoint_ratio(args, clk):
     """The differentiation workload: D3Q19 128^3, FP32-deviation forward, T = 1024, loss
     1/2 |phi(T) - target|^2, gradients w.r.t. phi0 and R(x) through torch.autograd."""
-    import torch
-
-    from paper_2410_13165_gb300 import LBM, build
-    from paper_2410_13165_gb300 import workloads as W
-    from paper_2410_13165_gb300.autograd import lbm_loss
+    from paper_2410_13165_gb300 import build
 
     build.build()
-    n, T = 128, 1024
-    X = W.node_coords(3, n, 0.0, 1.0 / n)
-    phi0 = torch.from_numpy(W.fourier_field(3, NMODES, SEED).value(X)).cuda()
-    R = torch.from_numpy(0.1 * W.fourier_field(3, 4, SEED + 10).value(X)).cuda()
-    target = torch.from_numpy(W.fourier_field(3, 8, SEED + 11).value(X)).cuda()
-    sim = LBM(3, n, u=U, precision="fp32dev")
-    times = {"forward": [], "backward": []}
-    for rep in range(3):
-        p, r = phi0.clone().requires_grad_(True), R.clone().requires_grad_(True)
-        torch.cuda.synchronize()
-        a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
-        a.record()
-        loss = lbm_loss(p, r, sim, T, target)
-        b.record()
-        loss.backward()
-        c.record()
-        torch.cuda.synchronize()
-        if rep:
-            times["forward"].append(a.elapsed_time(b))
-            times["backward"].append(b.elapsed_time(c))
-    fw, bw = float(np.mean(times["forward"])), float(np.mean(times["backward"]))
+    r = differentiation_workload(clk)
     print(json.dumps({"metric": "adjoint/forward time ratio, D3Q19 128^3 FP32-deviation, T=1024", "unit": "ratio",
-                      "value": bw / fw, "forward_ms": fw, "backward_ms": bw, "loss": float(loss),
-                      "note": "the scheme is affine in the state: the backward pass is T adjoint steps with no recomputation"}))
-    sim.close()
+                      "value": r["backward_over_forward"], **r, "clocks": clk.summary_windows()}))
     return 0
 
 
-def run_convergence(args):
+def run_convergence(args, clk):
     """Convergence slopes on the GPU at tau = 1/2 (periodic, K = 3): D2Q9 N = 16..128 (4 modes) and
     D3Q19 N = 32..256 (8 modes), FP64 and FP32-deviation; T = 1 (steps = N)."""
     import torch
@@ -549,11 +675,12 @@ def run_convergence(args):
                 sim.close()
             out["D%dQ%d_%s" % (d, 2 * d * d + 1, prec)] = {
                 "N": list(Ns), "rmse": errs, "slopes": [float(np.log2(a / b)) for a, b in zip(errs, errs[1:])]}
+    out.setdefault("clocks", clk.summary())
     print(json.dumps(out))
     return 0
 
 
-def run_fp32_floor(args):
+def run_fp32_floor(args, clk):
     """Where the FP32-deviation form stops converging at fourth order: periodic, tau = 1/2, K = 3,
     T = 1 (steps = N), RMSE against the exact solution for FP64 and FP32 deviations, D2Q9 N = 64..2048
     (4 modes) and D3Q19 N = 64..512 (8 modes). Fields of the large grids are generated on the host in
@@ -603,11 +730,12 @@ def run_fp32_floor(args):
         ratio = [b / a for a, b in zip(res["fp64"]["rmse"], res["fp32dev"]["rmse"])]
         res["fp32dev_over_fp64"] = ratio
         out["D%dQ%d" % (d, 2 * d * d + 1)] = res
+    out.setdefault("clocks", clk.summary())
     print(json.dumps(out))
     return 0
 
 
-def run_order_law(args):
+def run_order_law(args, clk):
     """Eq. (cr-estimation) on the GPU: convergence rates of the Dirichlet schemes against the boundary
     order P and the initialisation order K (2D, Example 1's setting with R = 5 and exact solutions of
     the wave family, T = 2; full-way at u = (0.1, 0.1), half-way at u = (0.01, 0.01); N = 20, 40, 80)."""
@@ -642,11 +770,12 @@ def run_order_law(args):
                 out["%s_P%d_K%d" % (bc, P, K)] = {
                     "rmse": errs, "rates": [float(np.log2(a / b)) for a, b in zip(errs, errs[1:])],
                     "law_min_K+1_P": min(K + 1, P)}
+    out.setdefault("clocks", clk.summary())
     print(json.dumps(out))
     return 0
 
 
-def run_examples(args):
+def run_examples(args, clk):
     """Example 2 (tanh bubble, periodic, 2D on [-1, 1]^2 and 3D on [-1/2, 1/2]^3) and Example 3's
     periodic 4D box: the total kinetic entropy sum_x sum_k f_k^2 / (2 omega_k) over time (conserved
     when every omega_k > 0, not for u = 0.4 (1, 1, 1, 1) in 4D), and the RMSE convergence rates at
@@ -717,11 +846,12 @@ def run_examples(args):
                 "N": list(Ns), "rmse": errs,
                 "rates": [float(np.log(a / b) / np.log(n2 / n1)) for a, b, n1, n2 in zip(errs, errs[1:], Ns, Ns[1:])]}
     out["rates"] = rates
+    out.setdefault("clocks", clk.summary())
     print(json.dumps(out))
     return 0
 
 
-def run_stability_map(args):
+def run_stability_map(args, clk):
     """Stability maps (Sec. 4) on the GPU: per velocity the smallest EDF weight (entropy conditions,
     Prop. 1) and the largest spectral radius of Eq. (G) over a xi grid (L2 conditions); the two
     regions are compared away from the boundary min omega = 0, as the paper states they coincide."""
@@ -750,6 +880,7 @@ def run_stability_map(args):
                         "agree_away_from_boundary": int(agree.sum()), "disagree": int((~agree).sum()),
                         "max_rho": float(np.max(rho)), "seconds": dt,
                         "matrices_per_second": len(S) * nxi ** d / dt}
+    out.setdefault("clocks", clk.summary())
     print(json.dumps(out))
     return 0
 
@@ -767,6 +898,7 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=100)
     ap.add_argument("--ref-n", type=int, default=128)
     ap.add_argument("--error-steps", type=int, default=2000)
+    ap.add_argument("--oracle-steps", type=int, default=50)
     ap.add_argument("--workload", default="d3q19_256",
                     choices=["d3q19_256", "d4q33_dirichlet", "d5q51_fp32dev", "adjoint", "convergence",
                              "order_law", "examples", "stability_map", "fp32_floor"])
@@ -779,7 +911,8 @@ def main():
     if args.workload in others:
         if args.steps == 400:
             args.steps = 50
-        return others[args.workload](args)
+        with ClockSampler(0) as clk:
+            return others[args.workload](args, clk)
     return run_ours(args)
 
 

@@ -83,6 +83,20 @@ typedef enum { LHE_M4_RULE = 0, LHE_M4_EXPLICIT = 1 } lhe_m4_mode;
  * for that step to complete before it touches global memory (same results, shorter gaps between
  * consecutive steps). The first kernel of a call is always ordered plainly behind the stream. */
 #define LHE_FLAG_NO_PDL 2
+/* LHE_FLAG_TEST_EXPIRE_WAIT: a test hook for the failure path of the staged FP32-deviation kernel. Its
+ * waits for copies are bounded (1 s); on expiry the kernel stops, waits (bounded) for the copies it
+ * has in flight, sets a host-visible flag and returns; once that kernel has finished, lhe_lbm_step,
+ * lhe_lbm_adjoint_step, lhe_lbm_macro and lhe_lbm_diagnostics (which synchronises, so it always sees
+ * it) report LHE_ERR_CUDA until lhe_lbm_init or lhe_lbm_set_state starts a new state. With this flag the handle's first staged launch gives its compute warps a zero
+ * limit, so that the path runs without any fault: that step stops early and leaves an invalid
+ * state. No effect on other handles or kernels. */
+#define LHE_FLAG_TEST_EXPIRE_WAIT 4
+/* LHE_FLAG_NO_FACE_ROWS: in the FP64 step of a Dirichlet box (d >= 2), treat the boundary nodes off the
+ * x_1 faces with the boundary-node kernel (one thread per node, the boundary data evaluated per node)
+ * instead of as whole rows with the interior rows' access pattern (the default). Same results: bit
+ * for bit with records of jets, to rounding with the exact-solution family (whose data the row form
+ * evaluates from coefficients separated in time). */
+#define LHE_FLAG_NO_FACE_ROWS 8
 
 typedef struct {
   int32_t d;              /* spatial dimension, 1..5 */
@@ -92,7 +106,7 @@ typedef struct {
   int32_t bc_order;       /* full-way: 1, 3 or 4 (Eq. (bun1)); half-way: 1..4 (Eq. (bun2)); unused if periodic */
   int32_t m4_mode;        /* lhe_m4_mode */
   int32_t allow_unstable; /* nonzero: accept weights with omega_k <= 0 (otherwise LHE_ERR_UNSTABLE) */
-  int32_t flags;          /* 0, or LHE_FLAG_* bits (kernel choices; results are identical) */
+  int32_t flags;          /* 0, or LHE_FLAG_* bits (kernel choices with identical results; a test hook) */
   int64_t n[LHE_MAX_DIM]; /* nodes per dimension (first d used); full-way n >= 3, otherwise n >= 3 */
   double lo[LHE_MAX_DIM]; /* box [lo, hi] per dimension */
   double hi[LHE_MAX_DIM];
@@ -239,15 +253,19 @@ LHE_API lhe_status lhe_lbm_diagnostics(lhe_lbm *lbm, double *out_host);
  * counterpart; this is a library service). For callers that cannot allocate at this point: code
  * whose device memory comes from a framework's allocator or a fixed budget, or that runs where the
  * CUDA runtime refuses cudaMalloc. It creates no handle and calls no allocating routine; its only
- * scratch memory is a 128 KiB array compiled into the library (one per device, alive until exit).
- *   p       : the lattice (d, n, lo, hi, bc, c, u, tau, R, m4 settings, stream); precision must be
- *             LHE_FP64. At most 268435456 nodes (4096 blocks of 65536 nodes fill the scratch array);
- *             larger lattices are rejected with LHE_ERR_ARG before anything is launched.
+ * scratch memory is a 128 KiB array compiled into the library (one per device, alive until exit),
+ * which holds the partial sums of at most 4096 reduction blocks.
+ *   p       : the lattice (d, n, lo, hi, bc, c, u, tau, R, m4 settings, allow_unstable, stream);
+ *             precision must be LHE_FP64. At most 268435456 nodes, the stated maximum of this entry
+ *             point: larger lattices are rejected with LHE_ERR_ARG before anything is launched. As
+ *             lhe_lbm_create, it returns LHE_ERR_UNSTABLE when some omega_k <= 0 unless
+ *             allow_unstable is set (the entropy then has terms of either sign).
  *   pop_dev : Q*S post-collision FP64 populations, k-major (what lhe_lbm_get_state writes for an
  *             LHE_FP64 handle); R_dev: per-site source (S doubles) or NULL for the constant p->R.
  *   out_dev : 4 doubles of device memory receiving the values of lhe_lbm_diagnostics, in order.
- * Asynchronous on p->stream. The first call on a device resolves the scratch array's device address
- * (cudaGetSymbolAddress); make that first call before any stream capture. Every call overwrites
+ * Asynchronous on p->stream. The scratch array's device address is looked up (cudaGetSymbolAddress)
+ * by the first call on a device, and again by the first call after the device's context was
+ * created anew (cudaDeviceReset); make those calls before any stream capture. Every call overwrites
  * the same scratch array, so calls whose kernels overlap on the GPU (other streams or threads) race;
  * order them on one stream. */
 LHE_API lhe_status lhe_lbm_diagnostics_noalloc(const lhe_lbm_params *p, const double *pop_dev, const double *R_dev,

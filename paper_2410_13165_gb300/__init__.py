@@ -24,7 +24,7 @@ _PREC = {"fp64": _abi.FP64, "fp32dev": _abi.FP32_DEV}
 
 def _params(d, n, lo=0.0, hi=1.0, u=None, R=0.0, tau=0.5, c=1.0, bc="periodic", bc_order=4, init_order=3,
             precision="fp64", g=0.5, m4=None, allow_unstable=False, stream=0, staged=True,
-            pdl=True) -> _abi.lhe_lbm_params:
+            pdl=True, flags=0) -> _abi.lhe_lbm_params:
     p = _abi.lhe_lbm_default_params()
     p.d = int(d)
     p.bc = _BC[bc]
@@ -32,7 +32,7 @@ def _params(d, n, lo=0.0, hi=1.0, u=None, R=0.0, tau=0.5, c=1.0, bc="periodic", 
     p.init_order = int(init_order)
     p.bc_order = int(bc_order)
     p.allow_unstable = int(bool(allow_unstable))
-    p.flags = (0 if staged else _abi.FLAG_NO_STAGING) | (0 if pdl else _abi.FLAG_NO_PDL)
+    p.flags = (0 if staged else _abi.FLAG_NO_STAGING) | (0 if pdl else _abi.FLAG_NO_PDL) | int(flags)
     ns = list(n) if hasattr(n, "__len__") else [n] * d
     los = list(lo) if hasattr(lo, "__len__") else [lo] * d
     his = list(hi) if hasattr(hi, "__len__") else [hi] * d
@@ -87,7 +87,8 @@ class LBM:
     """One lattice-Boltzmann problem on the current CUDA device (owns its population buffers)."""
 
     def __init__(self, d, n, lo=0.0, hi=1.0, u=None, R=0.0, tau=0.5, c=1.0, bc="periodic", bc_order=4,
-                 init_order=3, precision="fp64", g=0.5, m4=None, allow_unstable=False, staged=True, pdl=True):
+                 init_order=3, precision="fp64", g=0.5, m4=None, allow_unstable=False, staged=True, pdl=True,
+                 flags=0):
         import torch
 
         if not torch.cuda.is_available():
@@ -96,7 +97,7 @@ class LBM:
         self._torch = torch
         self.params = _params(d, n, lo, hi, u, R, tau, c, bc, bc_order, init_order, precision, g, m4,
                               allow_unstable, stream=torch.cuda.current_stream().cuda_stream, staged=staged,
-                              pdl=pdl)
+                              pdl=pdl, flags=flags)
         self.h = _abi.lhe_lbm_create(self.params)
         info = _abi.lhe_lbm_info(self.h)
         self.d, self.Q, self.S = info.d, info.Q, info.S

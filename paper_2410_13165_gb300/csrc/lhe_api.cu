@@ -116,7 +116,8 @@ lhe_status build_model(const lhe_lbm_params *p, Model &m, lhe_lbm *err_to) {
     return fail(err_to, LHE_ERR_ARG, "half-way bc_order must be 1..4");
   if (!(p->c > 0.0) || !std::isfinite(p->c)) return fail(err_to, LHE_ERR_ARG, "c must be positive");
   if (!(p->tau > 0.0) || !std::isfinite(p->tau)) return fail(err_to, LHE_ERR_ARG, "tau must be positive");
-  if (p->flags & ~(LHE_FLAG_NO_STAGING | LHE_FLAG_NO_PDL)) return fail(err_to, LHE_ERR_ARG, "unknown bits in flags");
+  if (p->flags & ~(LHE_FLAG_NO_STAGING | LHE_FLAG_NO_PDL | LHE_FLAG_TEST_EXPIRE_WAIT | LHE_FLAG_NO_FACE_ROWS))
+    return fail(err_to, LHE_ERR_ARG, "unknown bits in flags");
   if (p->m4_mode != LHE_M4_RULE && p->m4_mode != LHE_M4_EXPLICIT) return fail(err_to, LHE_ERR_ARG, "unknown m4_mode");
   if (p->m4_mode == LHE_M4_RULE && !(p->g >= 0.0 && p->g <= 1.0)) return fail(err_to, LHE_ERR_ARG, "g must be in [0, 1]");
   double dxs[kMaxD];
@@ -277,13 +278,108 @@ lhe_status unscale(lhe_lbm *l, int which) {
 // call reports it (the state is then incomplete).
 lhe_status check_pipeline(lhe_lbm *l) {
   if (l->tma_err_host && *(volatile int32_t *)l->tma_err_host)
-    return fail(l, LHE_ERR_CUDA, "a staged step kernel timed out waiting for its copies; the state is invalid");
+    return fail(l, LHE_ERR_CUDA, "a staged step kernel timed out waiting for its copies; the state is invalid "
+                                 "(lhe_lbm_init or lhe_lbm_set_state starts a new one)");
   return LHE_OK;
+}
+
+// A new state (init, set_state) clears a reported pipeline failure: once the stream has drained the
+// failed kernel, nothing can set the flag again.
+lhe_status clear_pipeline(lhe_lbm *l) {
+  if (l->tma_err_host && *(volatile int32_t *)l->tma_err_host) {
+    LHE_CK(l, cudaStreamSynchronize(l->stream));
+    *(volatile int32_t *)l->tma_err_host = 0;
+  }
+  return LHE_OK;
+}
+
+// The staged kernel's plan for the next launch; LHE_FLAG_TEST_EXPIRE_WAIT arms one launch whose compute
+// warps give up their first unready wait.
+DevTmaPlan staged_plan(lhe_lbm *l) {
+  DevTmaPlan p = l->tma;
+  if (l->tma_expire_armed) {
+    p.consumer_wait_ns = 0;
+    l->tma_expire_armed = false;
+  }
+  return p;
 }
 
 // Programmatic dependent launch between the consecutive step kernels of one step / adjoint_step call
 // (the first launch of a call keeps plain stream ordering behind whatever the caller queued).
 bool pdl_ok(const lhe_lbm *l) { return !(l->p.flags & LHE_FLAG_NO_PDL); }
+
+// Whether the exact-solution family's data use the face-row kernel (separable coefficients); record data
+// (jets, the manufactured solution) always do.
+constexpr bool kFamilyFaceRows = false;
+
+// The x_1-face part of the family's separable coefficients (after the face rows' part of fsep).
+double *xface_sep(const lhe_lbm *l) {
+  const size_t C = 1 + 2 * (size_t)l->wave.nmodes;
+  return l->fsep + ((size_t)l->nfslots * (size_t)l->p.n[0] + (size_t)l->nfrows * 2 * (2 * l->p.d - 1)) * C;
+}
+
+// The link k-bar with e_kbar = -e_k.
+int opposite_link(const lhe_lbm *l, int k) {
+  const int d = l->p.d;
+  for (int j = 0; j < l->Q; ++j) {
+    bool opp = true;
+    for (int i = 0; i < d; ++i)
+      if (l->e[j * d + i] != -l->e[k * d + i]) opp = false;
+    if (opp) return j;
+  }
+  return -1;
+}
+
+// The rows of a Dirichlet box with some of x_2..x_d on a face, in row order (see FaceRow), from the
+// boundary-node list `sites` (sorted by face signature, then site: the middle nodes of such a row
+// share a signature and follow one another).
+lhe_status build_face_rows(lhe_lbm *l, const Model &m, const std::vector<int32_t> &sites, std::vector<FaceRow> &rows) {
+  const int d = l->p.d;
+  const int64_t n1 = l->p.n[0];
+  int64_t nrows_all = 1;
+  for (int i = 1; i < d; ++i) nrows_all *= l->p.n[i];
+  std::vector<int32_t> index((size_t)nrows_all, -1);  // row -> face row
+  for (int64_t row = 0; row < nrows_all; ++row) {
+    int64_t r = row;
+    uint64_t mask = 0;
+    bool face = false;
+    for (int i = 1; i < d; ++i) {
+      const int64_t xi = r % l->p.n[i];
+      r /= l->p.n[i];
+      const int side = xi == 0 ? 1 : (xi == l->p.n[i] - 1 ? -1 : 0);
+      if (!side) continue;
+      face = true;
+      for (int k = 0; k < m.Q; ++k)
+        if (m.e[k * d + i] == side) mask |= 1ull << k;  // pull source x - e_k beyond that face
+    }
+    if (!face) continue;
+    FaceRow fr{};
+    fr.mask = mask;
+    fr.row = (int32_t)row;
+    fr.bmid = fr.blo = fr.bhi = -1;
+    index[(size_t)row] = (int32_t)rows.size();
+    rows.push_back(fr);
+  }
+  int64_t slots = 0;
+  for (FaceRow &fr : rows) {
+    fr.slot = (int32_t)slots;
+    slots += __builtin_popcountll(fr.mask);
+  }
+  if (slots * n1 > (int64_t)INT32_MAX) return fail(l, LHE_ERR_ARG, "too many face-row links");
+  l->nfslots = (int32_t)slots;
+  for (size_t j = 0; j < sites.size(); ++j) {
+    const int64_t row = sites[j] / n1, x1 = sites[j] % n1;
+    const int32_t f = index[(size_t)row];
+    if (f < 0) continue;  // an x_1-face node of an interior row
+    FaceRow &fr = rows[(size_t)f];
+    if (x1 == 0) fr.blo = (int32_t)j;
+    else if (x1 == n1 - 1) fr.bhi = (int32_t)j;
+    else if (x1 == 1) fr.bmid = (int32_t)j;
+  }
+  for (const FaceRow &fr : rows)
+    if (fr.blo < 0 || fr.bhi < 0 || fr.bmid < 0) return fail(l, LHE_ERR_ARG, "face rows: boundary list inconsistent");
+  return LHE_OK;
+}
 
 lhe_status check_handle(lhe_lbm *l) {
   if (!l) return fail(nullptr, LHE_ERR_ARG, "handle is NULL");
@@ -427,6 +523,17 @@ lhe_status lhe_lbm_create(const lhe_lbm_params *p, lhe_lbm **out) {
       const int64_t nrows = l->g.S_rows / l->g.n[0];
       e = cudaMalloc(&l->xface, sizeof(double) * (size_t)(2 * nrows * (2 * p->d - 1)));
       if (e != cudaSuccess) return bail(cuda_fail(l, e, "cudaMalloc(x-face boundary data)"));
+      if (p->d >= 2 && !(p->flags & LHE_FLAG_NO_FACE_ROWS)) {
+        std::vector<FaceRow> rows;
+        if (lhe_status st2 = build_face_rows(l, m, sites, rows)) return bail(st2);
+        l->nfrows = (int64_t)rows.size();
+        if (!rows.empty()) {
+          e = cudaMalloc(&l->frows, sizeof(FaceRow) * rows.size());
+          if (e != cudaSuccess) return bail(cuda_fail(l, e, "cudaMalloc(face rows)"));
+          e = cudaMemcpy(l->frows, rows.data(), sizeof(FaceRow) * rows.size(), cudaMemcpyHostToDevice);
+          if (e != cudaSuccess) return bail(cuda_fail(l, e, "cudaMemcpy(face rows)"));
+        }
+      }
     }
     e = cudaMalloc(&l->bsites, sizeof(int32_t) * sites.size());
     if (e != cudaSuccess) return bail(cuda_fail(l, e, "cudaMalloc(boundary nodes)"));
@@ -455,6 +562,7 @@ lhe_status lhe_lbm_create(const lhe_lbm_params *p, lhe_lbm **out) {
       e = prepare_dev3_tma(l->tma);
       if (e != cudaSuccess) return bail(cuda_fail(l, e, "shared-memory size of the staged step"));
       l->staged = true;
+      l->tma_expire_armed = (p->flags & LHE_FLAG_TEST_EXPIRE_WAIT) != 0;
     }
   }
   *out = l;
@@ -480,6 +588,8 @@ lhe_status lhe_lbm_destroy(lhe_lbm *l) {
   cudaFree(l->sp_R0);
   cudaFree(l->sp_rec0);
   cudaFree(l->xface);
+  cudaFree(l->frows);
+  cudaFree(l->fsep);
   cudaFree(l->bc_table);
   cudaFree(l->bc_axis);
   cudaFree(l->red_partials);
@@ -553,6 +663,7 @@ lhe_status lhe_lbm_init(lhe_lbm *l, const double *phi0, const double *grad, cons
   const size_t S = (size_t)l->g.S;
   if (!grad && l->p.init_order == 3 && l->p.bc != LHE_BC_PERIODIC)
     return fail(l, LHE_ERR_ARG, "Dirichlet boxes need an explicit grad phi0 for the third-order initialisation");
+  if (lhe_status st = clear_pipeline(l)) return st;
   l->Rnext_state = 0;
   if (Rf) {
     if (!l->Rfield) LHE_CK(l, cudaMalloc(&l->Rfield, sizeof(double) * S));
@@ -598,6 +709,8 @@ lhe_status lhe_lbm_init(lhe_lbm *l, const double *phi0, const double *grad, cons
   l->adj_ready = false;
   return LHE_OK;
 }
+
+static BoundaryArgs boundary_args(const lhe_lbm *l);
 
 lhe_status lhe_lbm_set_boundary_wave(lhe_lbm *l, const lhe_wave *w) {
   if (lhe_status s = check_handle(l)) return s;
@@ -682,6 +795,25 @@ lhe_status lhe_lbm_set_boundary_wave(lhe_lbm *l, const lhe_wave *w) {
   l->jet_mode = false;
   l->sp_mode = false;
   l->jet_ready = false;
+  l->fsep_ready = false;
+  if (l->frows && kFamilyFaceRows) {
+    // separable coefficients of these data on the face rows (k_step_face)
+    // layout: face-row slots, face-row ends, then the x_1-face nodes of the interior rows
+    const size_t C = 1 + 2 * (size_t)M;
+    const int64_t nrows_in = l->g.S_rows / l->g.n[0];
+    const size_t len = ((size_t)l->nfslots * (size_t)l->p.n[0] + (size_t)(l->nfrows + nrows_in) * 2 * (2 * d - 1)) * C;
+    if (len > l->fsep_len) {
+      LHE_CK(l, cudaFree(l->fsep));
+      l->fsep = nullptr;
+      l->fsep_len = 0;
+      LHE_CK(l, cudaMalloc(&l->fsep, sizeof(double) * len));
+      l->fsep_len = len;
+    }
+    BoundaryArgs b = boundary_args(l);
+    LHE_CK(l, launch_face_sep(d, l->p.bc, b, l->frows, l->nfrows, l->nfslots, l->fsep, l->stream));
+    LHE_CK(l, launch_xface_sep(d, l->p.bc, b, nrows_in, xface_sep(l), l->stream));
+    l->fsep_ready = true;
+  }
   return LHE_OK;
 }
 
@@ -987,12 +1119,30 @@ lhe_status lhe_lbm_step(lhe_lbm *l, int64_t n) {
     }
     // FP64 Dirichlet boxes: the row kernel also treats the x_1-face nodes of its rows
     const bool fused = !periodic && !dev && l->xface;
-    cudaError_t e = l->staged ? launch_step_dev3_tma(false, a, l->tma, l->stream)
-                    : fused       ? launch_step_box_fp64(d, l->p.bc, a, rest, l->xface, l->g.S_rows / l->g.n[0], l->stream)
+    const bool face_rows = fused && l->frows && (rest.rec != nullptr || l->fsep_ready);
+    if (face_rows && !rest.rec) {
+      // the family's data from separable coefficients: this step's term linear in t_eval per link
+      double gu = 0.0;
+      for (int i = 0; i < d; ++i) gu += l->wave.g[i] * l->p.u[i];
+      for (int k = 0; k < l->Q; ++k) {
+        const double wk = l->p.bc == LHE_BC_FULLWAY ? l->omega[k] : l->omega[k] + l->omega[opposite_link(l, k)];
+        rest.lt[k] = wk * (l->R - gu) * rest.t_eval;
+      }
+    }
+    cudaError_t e = l->staged ? launch_step_dev3_tma(false, a, staged_plan(l), l->stream)
+                    : fused       ? launch_step_box_fp64(d, l->p.bc, a, rest, l->xface,
+                                                         l->g.S_rows / l->g.n[0], face_rows && !rest.rec ? xface_sep(l) : nullptr,
+                                                         l->stream)
                     : dev         ? launch_step_dev(d, false, !periodic, a, l->stream)
                                   : launch_step_fp64(d, false, !periodic, a, l->stream);
     if (e != cudaSuccess) return cuda_fail(l, e, "step kernel launch");
-    if (!periodic) {
+    if (face_rows) {
+      // the other boundary nodes as whole rows: records over the whole node list, or the family's
+      // separable coefficients with this step's time terms
+      e = launch_step_face_fp64(d, l->p.bc, a, rest, l->frows, l->nfrows, l->nfslots, rest.rec ? nullptr : l->fsep,
+                                l->stream);
+      if (e != cudaSuccess) return cuda_fail(l, e, "face-row kernel launch");
+    } else if (!periodic) {
       if (fused) {  // the x_1-face-only nodes lead the list and are done
         rest.sites = b.sites + l->nb_xface;
         rest.nsites = b.nsites - l->nb_xface;
@@ -1011,6 +1161,7 @@ lhe_status lhe_lbm_macro(lhe_lbm *l, double *phi_out) {
   if (lhe_status s = check_handle(l)) return s;
   if (!phi_out) return fail(l, LHE_ERR_ARG, "phi_out is NULL");
   if (!l->initialised) return fail(l, LHE_ERR_STATE, "lhe_lbm_macro before lhe_lbm_init");
+  if (lhe_status st = check_pipeline(l)) return st;
   if (l->p.precision == LHE_FP32_DEV) {
     LHE_CK(l, launch_df_to_double(l->phi[l->cur], phi_out, l->g.S, l->stream));
     return LHE_OK;
@@ -1041,6 +1192,7 @@ lhe_status lhe_lbm_diagnostics(lhe_lbm *l, double *out_host) {
   LHE_CK(l, launch_reduce(l->p.d, l->p.precision == LHE_FP32_DEV, a, l->red_blocks, l->stream));
   LHE_CK(l, cudaMemcpyAsync(out_host, l->red_out, sizeof(double) * 4, cudaMemcpyDeviceToHost, l->stream));
   LHE_CK(l, cudaStreamSynchronize(l->stream));
+  if (lhe_status st = check_pipeline(l)) return st;  // the stream has drained: a failure is visible now
   if (out_host[3] > 0.0) return fail(l, LHE_ERR_NONFINITE, "non-finite values in the state");
   return LHE_OK;
 }
@@ -1062,6 +1214,7 @@ lhe_status lhe_lbm_set_state(lhe_lbm *l, const void *buf, int64_t step) {
   if (lhe_status s = check_handle(l)) return s;
   if (!buf) return fail(l, LHE_ERR_ARG, "buf is NULL");
   if (step < 0) return fail(l, LHE_ERR_ARG, "step must be >= 0");
+  if (lhe_status st = clear_pipeline(l)) return st;
   const size_t pb = pop_bytes(l);
   LHE_CK(l, cudaMemcpyAsync(l->pop[l->cur], buf, pb, cudaMemcpyDefault, l->stream));
   if (l->p.precision == LHE_FP32_DEV)
@@ -1122,7 +1275,7 @@ lhe_status lhe_lbm_adjoint_step(lhe_lbm *l, int64_t n) {
     a.phi_src = l->adjW[l->acur];
     a.phi_dst = l->adjW[1 - l->acur];
     a.pdl = it > 0 && pdl_ok(l);
-    cudaError_t e = l->staged ? launch_step_dev3_tma(true, a, l->tma, l->stream)
+    cudaError_t e = l->staged ? launch_step_dev3_tma(true, a, staged_plan(l), l->stream)
                     : dev         ? launch_step_dev(l->p.d, true, !periodic, a, l->stream)
                                   : launch_step_fp64(l->p.d, true, !periodic, a, l->stream);
     if (e != cudaSuccess) return cuda_fail(l, e, "adjoint step kernel launch");

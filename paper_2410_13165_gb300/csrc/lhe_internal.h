@@ -83,6 +83,7 @@ struct DevTmaPlan {
   FastDiv nx_div;
   int8_t ey[kMaxQ] = {}, ez[kMaxQ] = {};  // y and z components of e_k
   int32_t *err = nullptr;  // host-mapped flag, set when a pipeline wait timed out
+  uint64_t consumer_wait_ns = 1000000000ull;  // limit of the compute warps' waits (0: try once)
 };
 
 // FP64 collision forms for s != 2.
@@ -133,6 +134,22 @@ struct BoundaryArgs {
   double a[kMaxModes];
   double kappa[kMaxModes * kMaxD];
   double theta[kMaxModes];
+  // face rows with the family's data in separable form (k_step_face): the unknown population's data
+  // is P + lt_k + sum_m (A_m cos psi_m + B_m sin psi_m), psi_m = theta_m - kappa_m . u t_eval (ph_c, ph_s),
+  // lt_k the part linear in t_eval (one value per link and step)
+  double lt[kMaxQ];
+};
+
+// A row of a Dirichlet box (all x_1 at fixed x_2..x_d) with some x_2..x_d on a face: its nodes are
+// boundary nodes, stepped in row order by k_step_face (FP64 forward).
+struct FaceRow {
+  uint64_t mask;   // links unknown at every node of the row (pull source outside the box in x_2..x_d)
+  int32_t row;     // row index: the node x_1 = 0 is site row * n_1
+  int32_t bmid;    // position in the boundary-node list of the node x_1 = 1 (the row's middle nodes
+                   // follow it in order); blo / bhi: the nodes x_1 = 0 and x_1 = n_1 - 1
+  int32_t blo, bhi;
+  int32_t slot;    // unknown-link slots of the rows before this one (sum of their popcount(mask))
+  int32_t pad;
 };
 
 struct InitArgs {
@@ -186,8 +203,17 @@ cudaError_t launch_sp_jets(int d, const SineProductArgs &a, const double *pts, i
 cudaError_t launch_sp_source(const SineProductArgs &a, const Geom &g, double *R0, cudaStream_t st);
 cudaError_t launch_scale_field(const double *in, double scale, int64_t n, double *out, int sms, cudaStream_t st);
 cudaError_t launch_step_box_fp64(int d, int kind, const StepArgs &a, const BoundaryArgs &b, double *xb, int64_t nrows,
-                                 cudaStream_t st);
+                                 const double *xsep, cudaStream_t st);
+// Separable coefficients of the family's data at the x_1-face nodes of the interior rows (xsep != nullptr
+// in launch_step_box_fp64 selects them).
+cudaError_t launch_xface_sep(int d, int kind, const BoundaryArgs &b, int64_t nrows, double *xsep, cudaStream_t st);
 cudaError_t launch_adjoint_boundary(int d, int kind, bool dev, const BoundaryArgs &a, cudaStream_t st);
+// Face rows (FP64 forward): data from the records of jets (b.rec, b.roff over the whole node list)
+// or, sep != nullptr, from the family's separable coefficients (k_face_sep).
+cudaError_t launch_step_face_fp64(int d, int kind, const StepArgs &a, const BoundaryArgs &b, const FaceRow *rows,
+                                  int64_t nrows, int32_t nslots, const double *sep, cudaStream_t st);
+cudaError_t launch_face_sep(int d, int kind, const BoundaryArgs &b, const FaceRow *rows, int64_t nrows, int32_t nslots,
+                            double *sep, cudaStream_t st);
 cudaError_t launch_stability(int d, const double *omega_dev, int64_t npoints, int32_t nxi, double s,
                              unsigned long long *rho_bits_dev, cudaStream_t st);
 cudaError_t launch_init(int d, bool dev, const InitArgs &a, cudaStream_t st);
@@ -240,6 +266,14 @@ struct lhe_lbm {
   int64_t nb_xface = 0;         // leading entries of bsites on the x_1 faces only (other coordinates
                                 // interior): the FP64 forward step treats them in the row kernel
   double *xface = nullptr;      // their boundary data per step (2 (2d - 1) doubles per interior row)
+  // FP64 forward, d >= 2: the remaining boundary nodes as whole rows (k_step_face) unless
+  // LHE_FLAG_NO_FACE_ROWS; fsep: separable coefficients of the family's data on those rows
+  lhe::FaceRow *frows = nullptr;
+  int64_t nfrows = 0;
+  int32_t nfslots = 0;
+  double *fsep = nullptr;
+  size_t fsep_len = 0;
+  bool fsep_ready = false;
   bool have_wave = false;
   lhe_wave wave{};
   // boundary data as jets (lhe_lbm_set_boundary_jet), one step at a time
@@ -270,6 +304,7 @@ struct lhe_lbm {
   bool staged = false;
   lhe::DevTmaPlan tma{};
   int32_t *tma_err_host = nullptr;
+  bool tma_expire_armed = false; // LHE_FLAG_TEST_EXPIRE_WAIT: the next staged launch gives up its waits
   int32_t scale_j[2] = {0, 0};
   double scale_acc[2] = {0.0, 0.0};
   // diagnostics

@@ -1,5 +1,6 @@
 // lhe_misc.cu -- initialisation, finite-difference gradient, diagnostics reduction and the
 // adjoint seed / gradient kernels.
+#include "lhe_diag.cuh"
 #include "lhe_internal.h"
 #include "lhe_sites.cuh"
 
@@ -130,28 +131,6 @@ cudaError_t launch_fd_grad_transpose_add(int d, const Geom &g, double dx, const 
 // are used), the kinetic entropy sum_k f_k^2 / (2 omega_k) (Eq. (skfk)), |phi| and non-finite
 // values. Block partials go to a scratch array; a second single-block pass adds them in a fixed
 // order, so the result does not depend on scheduling.
-__device__ __forceinline__ void block_reduce4(double (&v)[4], double *sh) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    v[0] += __shfl_down_sync(0xffffffffu, v[0], o);
-    v[1] += __shfl_down_sync(0xffffffffu, v[1], o);
-    v[2] = fmax(v[2], __shfl_down_sync(0xffffffffu, v[2], o));
-    v[3] += __shfl_down_sync(0xffffffffu, v[3], o);
-  }
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  if (lane == 0)
-    for (int j = 0; j < 4; ++j) sh[wid * 4 + j] = v[j];
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    for (int w = 1; w < nw; ++w) {
-      v[0] += sh[w * 4 + 0];
-      v[1] += sh[w * 4 + 1];
-      v[2] = fmax(v[2], sh[w * 4 + 2]);
-      v[3] += sh[w * 4 + 3];
-    }
-  }
-}
-
 template <int D, bool DEV>
 __global__ void __launch_bounds__(256) k_reduce_partials(const ReduceArgs a) {
   constexpr int Q = Lattice<D>::Q;
@@ -162,8 +141,8 @@ __global__ void __launch_bounds__(256) k_reduce_partials(const ReduceArgs a) {
   for (int64_t site = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; site < S;
        site += (int64_t)gridDim.x * blockDim.x) {
     const double dtR = a.Rfield ? a.dt * a.Rfield[site] : a.dtR;
-    double phi, ent = 0.0, bad = 0.0;
     if (DEV) {
+      double phi, ent = 0.0, bad = 0.0;
       const float *g = static_cast<const float *>(a.pop);
       phi = df_value(a.phi[site]);
       if (!isfinite(phi)) bad += 1.0;
@@ -174,23 +153,13 @@ __global__ void __launch_bounds__(256) k_reduce_partials(const ReduceArgs a) {
         const double gk = recover ? (gs - a.omega[k] * dtR) / (1.0 - a.s) : gs;
         ent += gk * gk / (2.0 * a.omega[k]);
       }
+      v[0] += phi;
+      v[1] += ent;
+      v[2] = fmax(v[2], fabs(phi));
+      v[3] += bad;
     } else {
-      const double *f = static_cast<const double *>(a.pop);
-      double sum = 0.0;
-      for (int k = 0; k < Q; ++k) sum += f[k * S + site];
-      phi = sum - dtR;
-      const double psi = a.s * phi + dtR;
-      for (int k = 0; k < Q; ++k) {
-        const double fs = f[k * S + site];
-        if (!isfinite(fs)) bad += 1.0;
-        const double fk = recover ? (fs - a.omega[k] * psi) / (1.0 - a.s) : fs;
-        ent += fk * fk / (2.0 * a.omega[k]);
-      }
+      diag_site_fp64(static_cast<const double *>(a.pop), S, site, Q, a.omega, a.s, recover, dtR, v);
     }
-    v[0] += phi;
-    v[1] += ent;
-    v[2] = fmax(v[2], fabs(phi));
-    v[3] += bad;
   }
   block_reduce4(v, sh);
   if (threadIdx.x == 0)
@@ -200,16 +169,7 @@ __global__ void __launch_bounds__(256) k_reduce_partials(const ReduceArgs a) {
 __global__ void __launch_bounds__(256) k_reduce_final(const double *__restrict__ partials, int nblocks,
                                                       double *__restrict__ out) {
   __shared__ double sh[8 * 4];
-  double v[4] = {0.0, 0.0, 0.0, 0.0};
-  for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
-    v[0] += partials[b * 4 + 0];
-    v[1] += partials[b * 4 + 1];
-    v[2] = fmax(v[2], partials[b * 4 + 2]);
-    v[3] += partials[b * 4 + 3];
-  }
-  block_reduce4(v, sh);
-  if (threadIdx.x == 0)
-    for (int j = 0; j < 4; ++j) out[j] = v[j];
+  reduce_partials_final(partials, nblocks, out, sh);
 }
 
 template <int D>

@@ -6,9 +6,13 @@
 // needs a handle, and handles allocate; this entry point needs neither. Its only scratch memory
 // (the per-block partial sums of the reduction) lives in the file-scope device array below, which
 // exists from the moment the library is loaded on a device until the process exits.
+#include <cuda.h>  // CUcontext / CUresult types only; the driver call is reached through the runtime
+
+#include <algorithm>
 #include <mutex>
 #include <string>
 
+#include "lhe_diag.cuh"
 #include "lhe_internal.h"
 
 namespace lhe {
@@ -22,8 +26,8 @@ namespace lhe {
 namespace {
 
 constexpr int kNoAllocThreads = 256;
-constexpr int64_t kNoAllocSitesPerBlock = 65536;  // each block reduces one contiguous chunk of nodes
-constexpr int64_t kNoAllocMaxSites = kNoAllocSitesPerBlock * kNoAllocMaxBlocks;  // 268,435,456 nodes
+constexpr int kNoAllocBlocksPerSM = 4;
+constexpr int64_t kNoAllocMaxSites = int64_t(1) << 28;  // 268,435,456 nodes: the stated maximum
 
 struct NoAllocArgs {
   int64_t S;
@@ -34,93 +38,90 @@ struct NoAllocArgs {
   double s, dt, dtR;
 };
 
-__device__ __forceinline__ void reduce4(double (&v)[4], double *sh) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    v[0] += __shfl_down_sync(0xffffffffu, v[0], o);
-    v[1] += __shfl_down_sync(0xffffffffu, v[1], o);
-    v[2] = fmax(v[2], __shfl_down_sync(0xffffffffu, v[2], o));
-    v[3] += __shfl_down_sync(0xffffffffu, v[3], o);
-  }
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  if (lane == 0)
-    for (int j = 0; j < 4; ++j) sh[wid * 4 + j] = v[j];
-  __syncthreads();
-  if (threadIdx.x == 0)
-    for (int w = 1; w < nw; ++w) {
-      v[0] += sh[w * 4 + 0];
-      v[1] += sh[w * 4 + 1];
-      v[2] = fmax(v[2], sh[w * 4 + 2]);
-      v[3] += sh[w * 4 + 3];
-    }
-}
-
-// Block b reduces nodes [b * kNoAllocSitesPerBlock, min(S, (b + 1) * kNoAllocSitesPerBlock)) and
-// overwrites its own four partials, so nothing in the scratch array has to be cleared first.
-// Per node: phi = sum_k f*_k - dt R, the pre-collision populations recovered from
-// f* = (1 - s) f + omega (s phi + dt R) (post-collision values when s = 1), and the kinetic entropy
-// sum_k f_k^2 / (2 omega_k).
+// Grid-stride over the nodes; block b overwrites its own four partials, so nothing in the scratch
+// array has to be cleared first. The per-node formula is diag_site_fp64, as in the handle's kernel.
 __global__ void __launch_bounds__(kNoAllocThreads) k_noalloc_partials(const NoAllocArgs a, double *partials) {
   __shared__ double sh[(kNoAllocThreads / 32) * 4];
-  const int64_t begin = (int64_t)blockIdx.x * kNoAllocSitesPerBlock;
-  const int64_t end = min(a.S, begin + kNoAllocSitesPerBlock);
   const bool recover = a.s != 1.0;
   double v[4] = {0.0, 0.0, 0.0, 0.0};
-  for (int64_t site = begin + threadIdx.x; site < end; site += kNoAllocThreads) {
+  for (int64_t site = (int64_t)blockIdx.x * kNoAllocThreads + threadIdx.x; site < a.S;
+       site += (int64_t)gridDim.x * kNoAllocThreads) {
     const double dtR = a.Rfield ? a.dt * a.Rfield[site] : a.dtR;
-    double sum = 0.0, ent = 0.0, bad = 0.0;
-    for (int k = 0; k < a.Q; ++k) sum += a.pop[k * a.S + site];
-    const double phi = sum - dtR;
-    const double psi = a.s * phi + dtR;
-    for (int k = 0; k < a.Q; ++k) {
-      const double fs = a.pop[k * a.S + site];
-      if (!isfinite(fs)) bad += 1.0;
-      const double fk = recover ? (fs - a.omega[k] * psi) / (1.0 - a.s) : fs;
-      ent += fk * fk / (2.0 * a.omega[k]);
-    }
-    v[0] += phi;
-    v[1] += ent;
-    v[2] = fmax(v[2], fabs(phi));
-    v[3] += bad;
+    diag_site_fp64(a.pop, a.S, site, a.Q, a.omega, a.s, recover, dtR, v);
   }
-  reduce4(v, sh);
+  block_reduce4(v, sh);
   if (threadIdx.x == 0)
     for (int j = 0; j < 4; ++j) partials[blockIdx.x * 4 + j] = v[j];
 }
 
 __global__ void __launch_bounds__(kNoAllocThreads) k_noalloc_final(const double *partials, int nblocks, double *out) {
   __shared__ double sh[(kNoAllocThreads / 32) * 4];
-  double v[4] = {0.0, 0.0, 0.0, 0.0};
-  for (int b = threadIdx.x; b < nblocks; b += kNoAllocThreads) {
-    v[0] += partials[b * 4 + 0];
-    v[1] += partials[b * 4 + 1];
-    v[2] = fmax(v[2], partials[b * 4 + 2]);
-    v[3] += partials[b * 4 + 3];
-  }
-  reduce4(v, sh);
-  if (threadIdx.x == 0)
-    for (int j = 0; j < 4; ++j) out[j] = v[j];
+  reduce_partials_final(partials, nblocks, out, sh);
 }
 
-// Device address of the scratch array, resolved once per device (the host-side symbol is only a
-// stand-in and must never be handed to a kernel).
+// The scratch array's device address, per device. The host-side symbol g_noalloc_partials is only
+// a stand-in and must never be handed to a kernel. The address belongs to the context in which the
+// module was loaded: after cudaDeviceReset, or when the primary context is destroyed and created
+// again, the module is loaded anew and the array may sit elsewhere. So each entry remembers the
+// context it was resolved in (cuCtxGetId: unique for the life of the process) and is resolved
+// again whenever the current context differs.
 constexpr int kMaxDevices = 64;
+struct ScratchEntry {
+  unsigned long long ctx_id = 0;
+  double *ptr = nullptr;
+  int sms = 0;
+};
 std::mutex g_scratch_mu;
-double *g_scratch_ptr[kMaxDevices] = {};
+ScratchEntry g_scratch[kMaxDevices];
 
-cudaError_t scratch_for_current_device(double **out) {
+using CtxGetIdFn = CUresult(CUDAAPI *)(CUcontext, unsigned long long *);
+
+CtxGetIdFn ctx_get_id_fn() {
+  static CtxGetIdFn fn = [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      p = nullptr;
+    return reinterpret_cast<CtxGetIdFn>(p);
+  }();
+  return fn;
+}
+
+// Id of the current context, or 0 if none is current on this thread (yet).
+unsigned long long current_ctx_id() {
+  const CtxGetIdFn fn = ctx_get_id_fn();
+  unsigned long long id = 0;
+  if (!fn || fn(nullptr, &id) != CUDA_SUCCESS) return 0;
+  return id;
+}
+
+cudaError_t scratch_for_current_device(double **out, int *sms) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  if (!ctx_get_id_fn()) return cudaErrorNotSupported;
   std::lock_guard<std::mutex> lock(g_scratch_mu);
-  if (!g_scratch_ptr[dev]) {
+  ScratchEntry &ent = g_scratch[dev];
+  unsigned long long id = current_ctx_id();
+  if (id == 0 || id != ent.ctx_id || !ent.ptr) {
+    // cudaGetSymbolAddress also makes the device's primary context current on this thread when
+    // no context is, so the id is read (again) after it.
     void *p = nullptr;
     e = cudaGetSymbolAddress(&p, g_noalloc_partials);
     if (e != cudaSuccess) return e;
-    g_scratch_ptr[dev] = static_cast<double *>(p);
+    id = current_ctx_id();
+    if (id == 0) return cudaErrorDeviceUninitialized;  // "invalid device context"
+    int n = 0;
+    e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    ent.ctx_id = id;
+    ent.ptr = static_cast<double *>(p);
+    ent.sms = n;
   }
-  *out = g_scratch_ptr[dev];
+  *out = ent.ptr;
+  *sms = ent.sms;
   return cudaSuccess;
 }
 
@@ -133,21 +134,25 @@ extern "C" LHE_API lhe_status lhe_lbm_diagnostics_noalloc(const lhe_lbm_params *
   if (!p || !pop_dev || !out_dev) return record_error(LHE_ERR_ARG, "params, pop_dev and out_dev must not be NULL");
   if (p->precision != LHE_FP64)
     return record_error(LHE_ERR_ARG, "lhe_lbm_diagnostics_noalloc reads FP64 populations (precision LHE_FP64)");
+  const std::string prev_error = lhe_lbm_last_error(nullptr);
   double omega[kMaxQ];
   int32_t Q = 0;
   const lhe_status st = lhe_lbm_model(p, omega, nullptr, nullptr, &Q);
+  if (st == LHE_ERR_UNSTABLE && !p->allow_unstable) return st;  // as lhe_lbm_create: some omega_k <= 0
   if (st != LHE_OK && st != LHE_ERR_UNSTABLE) return st;
+  if (st == LHE_ERR_UNSTABLE) record_error(LHE_OK, prev_error);  // accepted: keep the caller's last error
   int64_t S = 1;
   for (int i = 0; i < p->d; ++i) {
     S *= p->n[i];
     if (S > kNoAllocMaxSites)
-      return record_error(LHE_ERR_ARG, "lhe_lbm_diagnostics_noalloc handles at most 268435456 lattice nodes "
-                                       "(4096 blocks of 65536 nodes in its fixed scratch array)");
+      return record_error(LHE_ERR_ARG, "lhe_lbm_diagnostics_noalloc handles at most 268435456 lattice nodes");
   }
   double *scratch = nullptr;
-  const cudaError_t se = scratch_for_current_device(&scratch);
+  int sms = 0;
+  const cudaError_t se = scratch_for_current_device(&scratch, &sms);
   if (se != cudaSuccess)
-    return record_error(LHE_ERR_CUDA, std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(se));
+    return record_error(LHE_ERR_CUDA, std::string("scratch address (cudaGetSymbolAddress / cuCtxGetId): ") +
+                                          cudaGetErrorString(se));
   NoAllocArgs a{};
   a.S = S;
   a.Q = Q;
@@ -159,7 +164,10 @@ extern "C" LHE_API lhe_status lhe_lbm_diagnostics_noalloc(const lhe_lbm_params *
   const double span = (p->bc == LHE_BC_FULLWAY) ? (double)(p->n[0] - 1) : (double)p->n[0];
   a.dt = (p->hi[0] - p->lo[0]) / span / p->c;
   a.dtR = a.dt * p->R;
-  const int nblocks = (int)((S + kNoAllocSitesPerBlock - 1) / kNoAllocSitesPerBlock);
+  int64_t nb = (S + kNoAllocThreads - 1) / kNoAllocThreads;
+  nb = std::min<int64_t>(nb, (int64_t)kNoAllocBlocksPerSM * std::max(sms, 1));
+  nb = std::max<int64_t>(1, std::min<int64_t>(nb, kNoAllocMaxBlocks));
+  const int nblocks = (int)nb;
   cudaStream_t stream = static_cast<cudaStream_t>(p->stream);
   k_noalloc_partials<<<nblocks, kNoAllocThreads, 0, stream>>>(a, scratch);
   k_noalloc_final<<<1, kNoAllocThreads, 0, stream>>>(scratch, nblocks, out_dev);

@@ -17,7 +17,8 @@
 // dependent launch).
 //
 // Every mbarrier wait is bounded in time; on expiry the kernel stops, records the failure in a
-// host-visible flag, waits (bounded) for its copies in flight and returns.
+// host-visible flag, waits (bounded) for its copies in flight and returns. Each warp takes the decision
+// to stop as a whole, so that no warp-wide operation runs with lanes missing.
 #include "lhe_internal.h"
 
 namespace lhe {
@@ -33,6 +34,12 @@ constexpr int kTmaThreads = 32 * (kConsumerWarps + 1);
 #define LHE_TMA_TILE_NODES 512
 #endif
 constexpr int kTileNodes = LHE_TMA_TILE_NODES;  // nodes per tile (whole rows, at most this many)
+#ifndef LHE_TMA_SMEM_BUDGET
+#define LHE_TMA_SMEM_BUDGET (200u * 1024u)
+#endif
+#ifndef LHE_TMA_MIN_BLOCKS
+#define LHE_TMA_MIN_BLOCKS 1
+#endif
 constexpr uint64_t kWaitLimitNs = 1000000000ull;  // 1 s per wait (a tile takes microseconds)
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -65,19 +72,38 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
   return ok != 0u;
 }
 
+// Non-blocking test of the phase (try_wait may suspend the thread for a while before it answers).
+__device__ __forceinline__ bool mbar_test_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n"
+      ".reg .pred p;\n"
+      "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      "selp.u32 %0, 1, 0, p;\n"
+      "}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0u;
+}
+
 __device__ __forceinline__ uint64_t global_ns() {
   uint64_t t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
 }
 
-// true once the phase with the given parity has completed; false after kWaitLimitNs (or 2^30 polls).
-__device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+// true once the phase with the given parity has completed; false after limit_ns (or 2^30 polls), or
+// as soon as *abort is set (abort may be null). limit_ns == 0 tests once without blocking (the test
+// hook of LHE_FLAG_TEST_EXPIRE_WAIT).
+__device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint64_t limit_ns, const volatile int *abort) {
+  if (limit_ns == 0) return mbar_test_wait(bar, parity);
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = global_ns();
   for (uint32_t it = 0; it < (1u << 30); ++it) {
     if (mbar_try_wait(bar, parity)) return true;
-    if (global_ns() - t0 > kWaitLimitNs) return false;
+    if (abort && *abort) return false;
+    if (global_ns() - t0 > limit_ns) return false;
   }
   return false;
 }
@@ -156,11 +182,11 @@ __device__ __forceinline__ void issue_tile(const StepArgs &a, const DevTmaPlan &
 
 }  // namespace
 
-// NXC: the row length n_1 when it is fixed at compile time (rows of 128 or 256 nodes, tiles of 512
-// nodes: R = 512 / NXC), so that the node index of a unit splits into row and x without a runtime
+// NXC: the row length n_1 when it is fixed at compile time (rows of 128 or 256 nodes, tiles of
+// kTileNodes nodes: R = kTileNodes / NXC), so that the node index of a unit splits into row and x without a runtime
 // division and the shared-memory offsets fold into constants; 0 for any other row length.
 template <bool ADJ, bool S2, int NXC>
-__global__ void __launch_bounds__(kTmaThreads, 1) k_step_dev3_tma(const StepArgs a, const DevTmaPlan p) {
+__global__ void __launch_bounds__(kTmaThreads, LHE_TMA_MIN_BLOCKS) k_step_dev3_tma(const StepArgs a, const DevTmaPlan p) {
   constexpr Lattice<3> L{};
   constexpr int Q = Lattice<3>::Q;
   extern __shared__ __align__(128) unsigned char smem[];
@@ -183,31 +209,36 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_step_dev3_tma(const StepArgs
   pdl_wait();  // the barriers are set up while the previous step finishes
   __syncthreads();
 
+  const volatile int *abort_v = &abort_flag;
   if (warp == kConsumerWarps) {
-    // producer warp: refill a stage as soon as every consumer warp has released it
+    // producer warp: refill a stage as soon as every consumer warp has released it. Lane 0 waits and
+    // decides; the decision is broadcast so that the warp leaves the loop as one.
     int i = 0;
     for (; i < my; ++i) {
       const int s = i % p.NS;
       const TileRef t = tile_ref(p, (int)blockIdx.x + i * (int)gridDim.x);
       if (i >= p.NS) {
-        bool ok = true;
-        if (lane == 0) ok = mbar_wait(smem_u32(&empty[s]), (uint32_t)((i / p.NS - 1) & 1));
-        ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
-        if (!ok || *(volatile int *)&abort_flag) {
-          if (lane == 0) abort_flag = 1;
+        int stop = 0;
+        if (lane == 0)
+          stop = !mbar_wait(smem_u32(&empty[s]), (uint32_t)((i / p.NS - 1) & 1), kWaitLimitNs, abort_v) || *abort_v;
+        if (__shfl_sync(0xffffffffu, stop, 0)) {
+          if (lane == 0) *(volatile int *)&abort_flag = 1;
           break;
         }
       }
       issue_tile<ADJ>(a, p, smem, smem_u32(&full[s]), t, s, lane);
     }
     if (lane == 0) {
-      if (*(volatile int *)&abort_flag) {
+      bool aborted = *abort_v != 0;
+      // leave only once the last stages have been consumed (bounded; given up if the consumers stop)
+      for (int j = max(0, my - p.NS); j < my && !aborted; ++j)
+        aborted = !mbar_wait(smem_u32(&empty[j % p.NS]), (uint32_t)((j / p.NS) & 1), kWaitLimitNs, abort_v);
+      if (aborted) {
         *p.err = 1;
-        // copies issued and possibly not consumed: wait for them (bounded) before leaving
-        for (int j = max(0, i - p.NS); j < i; ++j) mbar_wait(smem_u32(&full[j % p.NS]), (uint32_t)((j / p.NS) & 1));
-      } else {
-        // leave only once the last stages have been consumed (bounded)
-        for (int j = max(0, my - p.NS); j < my; ++j) mbar_wait(smem_u32(&empty[j % p.NS]), (uint32_t)((j / p.NS) & 1));
+        // the latest copies issued into each stage, possibly not consumed: wait for them (bounded)
+        // so that no copy into this CTA's shared memory is in flight when it exits
+        for (int j = max(0, i - p.NS); j < i; ++j)
+          mbar_wait(smem_u32(&full[j % p.NS]), (uint32_t)((j / p.NS) & 1), kWaitLimitNs, nullptr);
       }
     }
     __syncwarp();
@@ -218,16 +249,21 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_step_dev3_tma(const StepArgs
   // (the row length and tile height, constants where NXC fixes them, else read from the plan at each
   // use, so that the generic instantiation compiles as if NXC did not exist)
 #define LHE_NX (NXC ? NXC : p.nx)
-#define LHE_TILE_R (NXC ? 512 / NXC : p.R)
+#define LHE_TILE_R (NXC ? kTileNodes / NXC : p.R)
   const int sgn = ADJ ? -1 : 1;
   const int64_t S = a.g.S;
   const float oms = (float)a.oms;
   const bool field = !ADJ && a.Rfield != nullptr;
   for (int i = 0; i < my; ++i) {
     const int s = i % p.NS;
-    if (!mbar_wait(smem_u32(&full[s]), (uint32_t)((i / p.NS) & 1)) || *(volatile int *)&abort_flag) {
-      abort_flag = 1;
-      if (tid == 0) *p.err = 1;
+    // every lane waits on the barrier itself (each observes the copies' completion); the warp stops as
+    // one if any lane's wait gave up or another warp stopped
+    const bool ok = mbar_wait(smem_u32(&full[s]), (uint32_t)((i / p.NS) & 1), p.consumer_wait_ns, abort_v);
+    if (__any_sync(0xffffffffu, !ok || *abort_v)) {
+      if (lane == 0) {
+        *(volatile int *)&abort_flag = 1;
+        *p.err = 1;
+      }
       break;
     }
     const TileRef t = tile_ref(p, (int)blockIdx.x + i * (int)gridDim.x);
@@ -301,7 +337,7 @@ bool plan_dev3_tma(const Geom &g, int sms, DevTmaPlan &p) {
   const uint32_t phi_bytes = (uint32_t)(3 * (R + 2) * nx * 8);
   const uint32_t x_bytes = (uint32_t)(R * nx * 8);
   const uint32_t stage = g_bytes + phi_bytes + x_bytes;
-  const int NS = (int)std::min<uint32_t>((uint32_t)kTmaMaxStages, (200u * 1024u) / stage);
+  const int NS = (int)std::min<uint32_t>((uint32_t)kTmaMaxStages, (uint32_t)(LHE_TMA_SMEM_BUDGET) / stage);
   if (NS < 2) return false;
   constexpr Lattice<3> L{};
   p = DevTmaPlan{};
@@ -353,10 +389,10 @@ cudaError_t launch_step_dev3_tma(bool adjoint, const StepArgs &a, const DevTmaPl
   const bool s2 = a.s == 2.0;
   // Constant row lengths where they were measured faster: forward 128 and 256, adjoint 128 (the
   // adjoint with constant rows of 256 was 6 % slower than with the runtime ones).
-  auto kernel = (p.nx == 128 && p.R == 4)                ? pick_dev3_tma<128>(adjoint, s2)
-                : (!adjoint && p.nx == 256 && p.R == 2)  ? (s2 ? k_step_dev3_tma<false, true, 256>
-                                                               : k_step_dev3_tma<false, false, 256>)
-                                                         : pick_dev3_tma<0>(adjoint, s2);
+  auto kernel = (p.nx == 128 && p.R == kTileNodes / 128)              ? pick_dev3_tma<128>(adjoint, s2)
+                : (!adjoint && p.nx == 256 && p.R == kTileNodes / 256) ? (s2 ? k_step_dev3_tma<false, true, 256>
+                                                                              : k_step_dev3_tma<false, false, 256>)
+                                                                       : pick_dev3_tma<0>(adjoint, s2);
   return launch_kernel(kernel, p.grid, kTmaThreads, bytes, st, a.pdl != 0, a, p);
 }
 

@@ -111,7 +111,7 @@ def test_create_rejects_oversized_and_unknown_flag_arguments_before_touching_the
     assert ei.value.status == _abi.ERR_ARG
     assert b"2^31" in lib.lhe_lbm_last_error(None)
     q = _abi.lhe_lbm_default_params()
-    q.flags = 0x4
+    q.flags = 0x10  # bits 1, 2, 4 and 8 are defined
     with pytest.raises(_abi.LHEError) as ei:
         _abi.lhe_lbm_create(q)
     assert ei.value.status == _abi.ERR_ARG

@@ -80,7 +80,7 @@ def test_tanh_bubble_rates_2d():
     is sech^2(r0/(2W))/(4W) ~ 0.17, not 0, so the bubble has a cone tip at its centre and no scheme
     converges at fourth order in the RMSE there. The first-order initialisation gives the second-
     order rate of Table 2; the third-order one gives errors 10-15 times smaller, converging at ~1.7
-    (cone-limited; the same numbers as the oracle)."""
+    (cone-limited). On the coarsest grid both RMSEs equal the oracle's."""
     u = (0.1, 0.2)
     errs = {}
     for K in (1, 3):
@@ -95,6 +95,17 @@ def test_tanh_bubble_rates_2d():
             ex, _ = W.tanh_bubble(X, steps * sim.dt, u, -1.0, 1.0)
             errs[K].append(float(np.sqrt(np.mean((sim.macro().cpu().numpy() - ex) ** 2))))
             sim.close()
+    # the coarsest grid's RMSEs equal the oracle's
+    for K in (1, 3):
+        N = 200
+        X = W.node_coords(2, N, -1.0, 2.0 / N)
+        v, g = W.tanh_bubble(X, 0.0, u, -1.0, 1.0)
+        m = O.Model(2, N, -1.0, 1.0, u)
+        steps = int(round(1.0 / m.dt))
+        f = m.step(m.init(v, g, K), 0, steps)
+        ex, _ = W.tanh_bubble(X, steps * m.dt, u, -1.0, 1.0)
+        orc = O.rmse(m.phi(f), ex)
+        assert abs(errs[K][0] - orc) <= 1e-9 * orc, (K, errs[K][0], orc)
     r1 = [np.log2(a / b) for a, b in zip(errs[1], errs[1][1:])]
     r3 = [np.log2(a / b) for a, b in zip(errs[3], errs[3][1:])]
     assert all(1.8 < r < 2.3 for r in r1), (errs, r1)

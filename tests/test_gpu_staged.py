@@ -10,7 +10,7 @@ import numpy as np
 import pytest
 
 from oracle import oracle as O
-from paper_2410_13165_gb300 import LBM, build, workloads as W
+from paper_2410_13165_gb300 import LBM, LHEError, build, workloads as W
 from paper_2410_13165_gb300 import _abi
 
 pytestmark = pytest.mark.gpu
@@ -177,3 +177,47 @@ def test_staged_step_128_matches_register_kernel():
         res.append((sim.get_state().clone(), sim.macro().clone()))
         sim.close()
     assert torch.equal(res[0][0], res[1][0]) and torch.equal(res[0][1], res[1][1])
+
+
+@pytest.mark.parametrize("adjoint", [False, True])
+def test_wait_expiry_is_reported_and_a_new_state_recovers(adjoint):
+    """The failure path of the staged kernel, run without any fault: LHE_FLAG_TEST_EXPIRE_WAIT gives the
+    compute warps of the handle's first staged launch a zero wait limit, so they give up on copies
+    still in flight. The kernel must return (the producer warp waits, bounded, for the copies it
+    issued), the next calls must report LHE_ERR_CUDA, and a new state (lhe_lbm_init) must clear the
+    report and step exactly like a handle that never failed."""
+    import torch
+
+    n = (64, 64, 64)
+    hi = [ni / 32.0 for ni in n]
+    v, g = _problem(n, 70)
+    kw = dict(u=(0.1, -0.05, 0.08), tau=0.8, precision="fp32dev")
+    ref = LBM(3, n, 0.0, hi, **kw)
+    sim = LBM(3, n, 0.0, hi, flags=_abi.FLAG_TEST_EXPIRE_WAIT, **kw)
+    for s in (ref, sim):
+        s.init(_t(v), _t(g))
+    if adjoint:
+        sim.adjoint_seed(sim.macro())
+        sim.adjoint_step(1)          # the armed launch: the adjoint kernel gives up
+    else:
+        sim.step(1)                  # the armed launch: the forward kernel gives up
+    torch.cuda.synchronize()         # the kernel returned
+    for call in ((lambda: sim.adjoint_step(1)) if adjoint else (lambda: sim.step(1)), sim.macro, sim.diagnostics):
+        with pytest.raises(LHEError) as ei:
+            call()
+        assert ei.value.status == _abi.ERR_CUDA and "timed out" in str(ei.value)
+    # a new state clears the report; the hook was one launch only
+    sim.init(_t(v), _t(g))
+    for s in (ref, sim):
+        s.step(5)
+    assert torch.equal(sim.get_state(), ref.get_state())
+    if adjoint:
+        for s in (ref, sim):
+            s.adjoint_seed(s.macro())
+            s.adjoint_step(4)
+        gs = [s.adjoint_grads(want_grad=True, want_R=True) for s in (ref, sim)]
+        for a, b in zip(gs[0], gs[1]):
+            assert torch.equal(a, b)
+    assert sim.diagnostics()["ok"]
+    ref.close()
+    sim.close()

@@ -91,12 +91,14 @@ typedef enum { LHE_M4_RULE = 0, LHE_M4_EXPLICIT = 1 } lhe_m4_mode;
  * limit, so that the path runs without any fault: that step stops early and leaves an invalid
  * state. No effect on other handles or kernels. */
 #define LHE_FLAG_TEST_EXPIRE_WAIT 4
-/* LHE_FLAG_NO_FACE_ROWS: in the FP64 step of a Dirichlet box (d >= 2), treat the boundary nodes off the
- * x_1 faces with the boundary-node kernel (one thread per node, the boundary data evaluated per node)
- * instead of as whole rows with the interior rows' access pattern (the default). Same results: bit
- * for bit with records of jets, to rounding with the exact-solution family (whose data the row form
- * evaluates from coefficients separated in time). */
-#define LHE_FLAG_NO_FACE_ROWS 8
+/* LHE_FLAG_NODE_BOUNDARY: in the FP64 step of a Dirichlet box, treat the boundary nodes with the
+ * boundary-node kernels (the x_1-face nodes in the lanes of their rows, the others one thread per node
+ * with the boundary data evaluated per node) instead of stepping the whole box as rows that take the
+ * unknown populations from a dense array of the step's boundary data (the default, which holds one
+ * more array of Q*S doubles). Same results: bit for bit with records of jets or the manufactured
+ * solution, to rounding with the exact-solution family (whose data the dense form evaluates from
+ * coefficients separated in time). */
+#define LHE_FLAG_NODE_BOUNDARY 8
 
 typedef struct {
   int32_t d;              /* spatial dimension, 1..5 */

@@ -24,7 +24,7 @@ M4_RULE, M4_EXPLICIT = 0, 1
 FLAG_NO_STAGING = 1
 FLAG_NO_PDL = 2
 FLAG_TEST_EXPIRE_WAIT = 4  # test hook: the first staged launch of a handle takes its wait-timeout path
-FLAG_NO_FACE_ROWS = 8
+FLAG_NODE_BOUNDARY = 8
 
 # every entry point declared in include/lhe_lbm.h
 EXPORTS = [

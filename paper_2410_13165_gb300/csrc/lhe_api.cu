@@ -116,7 +116,7 @@ lhe_status build_model(const lhe_lbm_params *p, Model &m, lhe_lbm *err_to) {
     return fail(err_to, LHE_ERR_ARG, "half-way bc_order must be 1..4");
   if (!(p->c > 0.0) || !std::isfinite(p->c)) return fail(err_to, LHE_ERR_ARG, "c must be positive");
   if (!(p->tau > 0.0) || !std::isfinite(p->tau)) return fail(err_to, LHE_ERR_ARG, "tau must be positive");
-  if (p->flags & ~(LHE_FLAG_NO_STAGING | LHE_FLAG_NO_PDL | LHE_FLAG_TEST_EXPIRE_WAIT | LHE_FLAG_NO_FACE_ROWS))
+  if (p->flags & ~(LHE_FLAG_NO_STAGING | LHE_FLAG_NO_PDL | LHE_FLAG_TEST_EXPIRE_WAIT | LHE_FLAG_NODE_BOUNDARY))
     return fail(err_to, LHE_ERR_ARG, "unknown bits in flags");
   if (p->m4_mode != LHE_M4_RULE && p->m4_mode != LHE_M4_EXPLICIT) return fail(err_to, LHE_ERR_ARG, "unknown m4_mode");
   if (p->m4_mode == LHE_M4_RULE && !(p->g >= 0.0 && p->g <= 1.0)) return fail(err_to, LHE_ERR_ARG, "g must be in [0, 1]");
@@ -308,16 +308,6 @@ DevTmaPlan staged_plan(lhe_lbm *l) {
 // (the first launch of a call keeps plain stream ordering behind whatever the caller queued).
 bool pdl_ok(const lhe_lbm *l) { return !(l->p.flags & LHE_FLAG_NO_PDL); }
 
-// Whether the exact-solution family's data use the face-row kernel (separable coefficients); record data
-// (jets, the manufactured solution) always do.
-constexpr bool kFamilyFaceRows = false;
-
-// The x_1-face part of the family's separable coefficients (after the face rows' part of fsep).
-double *xface_sep(const lhe_lbm *l) {
-  const size_t C = 1 + 2 * (size_t)l->wave.nmodes;
-  return l->fsep + ((size_t)l->nfslots * (size_t)l->p.n[0] + (size_t)l->nfrows * 2 * (2 * l->p.d - 1)) * C;
-}
-
 // The link k-bar with e_kbar = -e_k.
 int opposite_link(const lhe_lbm *l, int k) {
   const int d = l->p.d;
@@ -328,57 +318,6 @@ int opposite_link(const lhe_lbm *l, int k) {
     if (opp) return j;
   }
   return -1;
-}
-
-// The rows of a Dirichlet box with some of x_2..x_d on a face, in row order (see FaceRow), from the
-// boundary-node list `sites` (sorted by face signature, then site: the middle nodes of such a row
-// share a signature and follow one another).
-lhe_status build_face_rows(lhe_lbm *l, const Model &m, const std::vector<int32_t> &sites, std::vector<FaceRow> &rows) {
-  const int d = l->p.d;
-  const int64_t n1 = l->p.n[0];
-  int64_t nrows_all = 1;
-  for (int i = 1; i < d; ++i) nrows_all *= l->p.n[i];
-  std::vector<int32_t> index((size_t)nrows_all, -1);  // row -> face row
-  for (int64_t row = 0; row < nrows_all; ++row) {
-    int64_t r = row;
-    uint64_t mask = 0;
-    bool face = false;
-    for (int i = 1; i < d; ++i) {
-      const int64_t xi = r % l->p.n[i];
-      r /= l->p.n[i];
-      const int side = xi == 0 ? 1 : (xi == l->p.n[i] - 1 ? -1 : 0);
-      if (!side) continue;
-      face = true;
-      for (int k = 0; k < m.Q; ++k)
-        if (m.e[k * d + i] == side) mask |= 1ull << k;  // pull source x - e_k beyond that face
-    }
-    if (!face) continue;
-    FaceRow fr{};
-    fr.mask = mask;
-    fr.row = (int32_t)row;
-    fr.bmid = fr.blo = fr.bhi = -1;
-    index[(size_t)row] = (int32_t)rows.size();
-    rows.push_back(fr);
-  }
-  int64_t slots = 0;
-  for (FaceRow &fr : rows) {
-    fr.slot = (int32_t)slots;
-    slots += __builtin_popcountll(fr.mask);
-  }
-  if (slots * n1 > (int64_t)INT32_MAX) return fail(l, LHE_ERR_ARG, "too many face-row links");
-  l->nfslots = (int32_t)slots;
-  for (size_t j = 0; j < sites.size(); ++j) {
-    const int64_t row = sites[j] / n1, x1 = sites[j] % n1;
-    const int32_t f = index[(size_t)row];
-    if (f < 0) continue;  // an x_1-face node of an interior row
-    FaceRow &fr = rows[(size_t)f];
-    if (x1 == 0) fr.blo = (int32_t)j;
-    else if (x1 == n1 - 1) fr.bhi = (int32_t)j;
-    else if (x1 == 1) fr.bmid = (int32_t)j;
-  }
-  for (const FaceRow &fr : rows)
-    if (fr.blo < 0 || fr.bhi < 0 || fr.bmid < 0) return fail(l, LHE_ERR_ARG, "face rows: boundary list inconsistent");
-  return LHE_OK;
 }
 
 lhe_status check_handle(lhe_lbm *l) {
@@ -523,16 +462,74 @@ lhe_status lhe_lbm_create(const lhe_lbm_params *p, lhe_lbm **out) {
       const int64_t nrows = l->g.S_rows / l->g.n[0];
       e = cudaMalloc(&l->xface, sizeof(double) * (size_t)(2 * nrows * (2 * p->d - 1)));
       if (e != cudaSuccess) return bail(cuda_fail(l, e, "cudaMalloc(x-face boundary data)"));
-      if (p->d >= 2 && !(p->flags & LHE_FLAG_NO_FACE_ROWS)) {
-        std::vector<FaceRow> rows;
-        if (lhe_status st2 = build_face_rows(l, m, sites, rows)) return bail(st2);
-        l->nfrows = (int64_t)rows.size();
-        if (!rows.empty()) {
-          e = cudaMalloc(&l->frows, sizeof(FaceRow) * rows.size());
-          if (e != cudaSuccess) return bail(cuda_fail(l, e, "cudaMalloc(face rows)"));
-          e = cudaMemcpy(l->frows, rows.data(), sizeof(FaceRow) * rows.size(), cudaMemcpyHostToDevice);
-          if (e != cudaSuccess) return bail(cuda_fail(l, e, "cudaMemcpy(face rows)"));
+      if (!(p->flags & LHE_FLAG_NODE_BOUNDARY)) {
+        // the step's boundary data: the entries (unknown link k of boundary node x) whose link leaves
+        // through a face of x_2..x_d, sorted by k then x, in a dense array shaped like the populations;
+        // then those through an x_1 face only, sorted by x then k, compact per row end; with the record
+        // (node-major, as broff) that feeds each
+        struct Ent {
+          int cls;
+          long long key1, key2;
+          int32_t rec;
+          bool operator<(const Ent &o) const {
+            return cls != o.cls ? cls < o.cls : (key1 != o.key1 ? key1 < o.key1 : key2 < o.key2);
+          }
+        };
+        std::vector<Ent> ent;
+        ent.reserve((size_t)nrec);
+        for (size_t j = 0; j < sites.size(); ++j) {
+          int32_t r = l->broff_host[j];
+          for (int k = 0; k < m.Q; ++k) {
+            bool row = false, xo = false;
+            int32_t ws = keyed[j].first;
+            for (int i = 0; i < p->d; ++i, ws /= 3) {
+              const int e_ki = m.e[k * p->d + i];
+              const bool out = (ws % 3 == 1 && e_ki == 1) || (ws % 3 == 2 && e_ki == -1);
+              if (out && i > 0) row = true;
+              if (out && i == 0) xo = true;
+            }
+            if (row) ent.push_back(Ent{0, k, sites[j], r++});
+            else if (xo) ent.push_back(Ent{1, sites[j], k, r++});
+          }
         }
+        std::sort(ent.begin(), ent.end());
+        std::vector<long long> ek(ent.size()), ed(ent.size()), eo(ent.size());
+        std::vector<int32_t> er(ent.size());  // record (node-major) -> entry
+        const int J = 2 * p->d - 1;
+        const int64_t n1 = p->n[0];
+        for (size_t i = 0; i < ent.size(); ++i) {
+          const long long k = ent[i].cls == 0 ? ent[i].key1 : ent[i].key2;
+          const long long x = ent[i].cls == 0 ? ent[i].key2 : ent[i].key1;
+          ek[i] = (k << 32) | x;
+          er[(size_t)ent[i].rec] = (int32_t)i;
+          int kb = 0, jx = 0;
+          const int side = (x % n1) == 0 ? 1 : -1;
+          for (int q = 0; q < m.Q; ++q) {
+            bool opp = true;
+            for (int dd = 0; dd < p->d; ++dd)
+              if (m.e[q * p->d + dd] != -m.e[k * p->d + dd]) opp = false;
+            if (opp) kb = q;
+            if (q < k && m.e[q * p->d] == side) ++jx;
+          }
+          ed[i] = ent[i].cls == 0 ? k * S + x : (long long)m.Q * S + (2 * (x / n1) + (side > 0 ? 0 : 1)) * J + jx;
+          eo[i] = (long long)kb * S + x;
+        }
+        int64_t nrows_all = 1;
+        for (int i = 1; i < p->d; ++i) nrows_all *= p->n[i];
+        e = cudaMalloc(&l->bdata, pop_bytes(l) + sizeof(double) * (size_t)nrows_all * 2 * J);
+        if (e == cudaSuccess) e = cudaMalloc(&l->bdst, sizeof(long long) * std::max<size_t>(ed.size(), 1));
+        if (e == cudaSuccess) e = cudaMalloc(&l->bopp, sizeof(long long) * std::max<size_t>(eo.size(), 1));
+        if (e == cudaSuccess && !ed.empty())
+          e = cudaMemcpy(l->bdst, ed.data(), sizeof(long long) * ed.size(), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess && !eo.empty())
+          e = cudaMemcpy(l->bopp, eo.data(), sizeof(long long) * eo.size(), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMalloc(&l->bent, sizeof(long long) * std::max<size_t>(ek.size(), 1));
+        if (e == cudaSuccess) e = cudaMalloc(&l->bmap, sizeof(int32_t) * std::max<size_t>(er.size(), 1));
+        if (e == cudaSuccess && !ek.empty())
+          e = cudaMemcpy(l->bent, ek.data(), sizeof(long long) * ek.size(), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess && !er.empty())
+          e = cudaMemcpy(l->bmap, er.data(), sizeof(int32_t) * er.size(), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return bail(cuda_fail(l, e, "dense boundary data"));
       }
     }
     e = cudaMalloc(&l->bsites, sizeof(int32_t) * sites.size());
@@ -588,7 +585,11 @@ lhe_status lhe_lbm_destroy(lhe_lbm *l) {
   cudaFree(l->sp_R0);
   cudaFree(l->sp_rec0);
   cudaFree(l->xface);
-  cudaFree(l->frows);
+  cudaFree(l->bdata);
+  cudaFree(l->bent);
+  cudaFree(l->bmap);
+  cudaFree(l->bdst);
+  cudaFree(l->bopp);
   cudaFree(l->fsep);
   cudaFree(l->bc_table);
   cudaFree(l->bc_axis);
@@ -711,6 +712,7 @@ lhe_status lhe_lbm_init(lhe_lbm *l, const double *phi0, const double *grad, cons
 }
 
 static BoundaryArgs boundary_args(const lhe_lbm *l);
+static lhe_status ensure_jet_buffers(lhe_lbm *l);
 
 lhe_status lhe_lbm_set_boundary_wave(lhe_lbm *l, const lhe_wave *w) {
   if (lhe_status s = check_handle(l)) return s;
@@ -795,13 +797,9 @@ lhe_status lhe_lbm_set_boundary_wave(lhe_lbm *l, const lhe_wave *w) {
   l->jet_mode = false;
   l->sp_mode = false;
   l->jet_ready = false;
-  l->fsep_ready = false;
-  if (l->frows && kFamilyFaceRows) {
-    // separable coefficients of these data on the face rows (k_step_face)
-    // layout: face-row slots, face-row ends, then the x_1-face nodes of the interior rows
-    const size_t C = 1 + 2 * (size_t)M;
-    const int64_t nrows_in = l->g.S_rows / l->g.n[0];
-    const size_t len = ((size_t)l->nfslots * (size_t)l->p.n[0] + (size_t)(l->nfrows + nrows_in) * 2 * (2 * d - 1)) * C;
+  if (l->bdata) {
+    // the family's data separated in time, per entry of the dense array
+    const size_t len = (size_t)std::max<int64_t>(l->nrec, 1) * (1 + 2 * (size_t)M);
     if (len > l->fsep_len) {
       LHE_CK(l, cudaFree(l->fsep));
       l->fsep = nullptr;
@@ -810,9 +808,7 @@ lhe_status lhe_lbm_set_boundary_wave(lhe_lbm *l, const lhe_wave *w) {
       l->fsep_len = len;
     }
     BoundaryArgs b = boundary_args(l);
-    LHE_CK(l, launch_face_sep(d, l->p.bc, b, l->frows, l->nfrows, l->nfslots, l->fsep, l->stream));
-    LHE_CK(l, launch_xface_sep(d, l->p.bc, b, nrows_in, xface_sep(l), l->stream));
-    l->fsep_ready = true;
+    LHE_CK(l, launch_family_sep(d, l->p.bc, b, l->bent, l->nrec, l->fsep, l->stream));
   }
   return LHE_OK;
 }
@@ -945,6 +941,7 @@ lhe_status lhe_lbm_set_boundary_jet(lhe_lbm *l, const double *jet_dev) {
   if (lhe_status st = ensure_jet_buffers(l)) return st;
   BoundaryArgs b = boundary_args(l);
   b.roff = l->broff;  // the kernel writes l->brec; b.rec stays null (the data are being formed)
+  b.rmap = l->bmap;   // in the order of the dense entries when the handle has them
   // the schemes' R terms (a source varying in time): full-way at the new time t_{n+1} (the source of
   // this step's collision), half-way at t_n (the source of the collision of f*_kbar)
   b.Rfield = l->p.bc == LHE_BC_FULLWAY ? next_source(l) : l->Rfield;
@@ -1018,6 +1015,7 @@ lhe_status lhe_lbm_set_boundary_sine_product(lhe_lbm *l, const lhe_sine_product 
   if (e == cudaSuccess) {
     BoundaryArgs b = boundary_args(l);
     b.roff = l->broff;
+    b.rmap = l->bmap;
     b.Rfield = l->sp_R0;  // data and source share the time factor in both schemes
     e = launch_jet_records(d, l->p.bc, b, djet, jet_index_table(d).data(), l->sp_rec0, l->stream);
   }
@@ -1117,39 +1115,42 @@ lhe_status lhe_lbm_step(lhe_lbm *l, int64_t n) {
         l->jet_ready = false;
       }
     }
-    // FP64 Dirichlet boxes: the row kernel also treats the x_1-face nodes of its rows
-    const bool fused = !periodic && !dev && l->xface;
-    const bool face_rows = fused && l->frows && (rest.rec != nullptr || l->fsep_ready);
-    if (face_rows && !rest.rec) {
-      // the family's data from separable coefficients: this step's term linear in t_eval per link
-      double gu = 0.0;
-      for (int i = 0; i < d; ++i) gu += l->wave.g[i] * l->p.u[i];
-      for (int k = 0; k < l->Q; ++k) {
-        const double wk = l->p.bc == LHE_BC_FULLWAY ? l->omega[k] : l->omega[k] + l->omega[opposite_link(l, k)];
-        rest.lt[k] = wk * (l->R - gu) * rest.t_eval;
+    // FP64 Dirichlet boxes: the whole box as rows with dense boundary data (default), or the interior
+    // rows with their x_1-face nodes and then the other boundary nodes one by one (LHE_FLAG_NODE_BOUNDARY)
+    const bool dense = !periodic && !dev && l->bdata;
+    const bool fused = !periodic && !dev && l->xface && !dense;
+    cudaError_t e = cudaSuccess;
+    if (dense) {
+      // this step's unknown populations into the dense array, then the whole box
+      if (!rest.rec) {
+        // the exact-solution family: this step's term linear in t_eval per link
+        double gu = 0.0;
+        for (int i = 0; i < d; ++i) gu += l->wave.g[i] * l->p.u[i];
+        for (int k = 0; k < l->Q; ++k) {
+          const double wk = l->p.bc == LHE_BC_FULLWAY ? l->omega[k] : l->omega[k] + l->omega[opposite_link(l, k)];
+          rest.lt[k] = wk * (l->R - gu) * rest.t_eval;
+        }
       }
-    }
-    cudaError_t e = l->staged ? launch_step_dev3_tma(false, a, staged_plan(l), l->stream)
-                    : fused       ? launch_step_box_fp64(d, l->p.bc, a, rest, l->xface,
-                                                         l->g.S_rows / l->g.n[0], face_rows && !rest.rec ? xface_sep(l) : nullptr,
-                                                         l->stream)
-                    : dev         ? launch_step_dev(d, false, !periodic, a, l->stream)
-                                  : launch_step_fp64(d, false, !periodic, a, l->stream);
-    if (e != cudaSuccess) return cuda_fail(l, e, "step kernel launch");
-    if (face_rows) {
-      // the other boundary nodes as whole rows: records over the whole node list, or the family's
-      // separable coefficients with this step's time terms
-      e = launch_step_face_fp64(d, l->p.bc, a, rest, l->frows, l->nfrows, l->nfslots, rest.rec ? nullptr : l->fsep,
-                                l->stream);
-      if (e != cudaSuccess) return cuda_fail(l, e, "face-row kernel launch");
-    } else if (!periodic) {
-      if (fused) {  // the x_1-face-only nodes lead the list and are done
-        rest.sites = b.sites + l->nb_xface;
-        rest.nsites = b.nsites - l->nb_xface;
-        if (rest.roff) rest.roff += l->nb_xface;
+      e = launch_bdata_step(l->p.bc, rest.rec != nullptr, rest, l->bent, l->bdst, l->bopp, l->nrec,
+                            rest.rec ? rest.rec : l->fsep, l->bdata, l->stream);
+      if (e != cudaSuccess) return cuda_fail(l, e, "boundary data kernel launch");
+      e = launch_step_box_dense(d, a, l->bdata, l->stream);
+      if (e != cudaSuccess) return cuda_fail(l, e, "step kernel launch");
+    } else {
+      e = l->staged ? launch_step_dev3_tma(false, a, staged_plan(l), l->stream)
+          : fused   ? launch_step_box_fp64(d, l->p.bc, a, rest, l->xface, l->g.S_rows / l->g.n[0], l->stream)
+          : dev     ? launch_step_dev(d, false, !periodic, a, l->stream)
+                    : launch_step_fp64(d, false, !periodic, a, l->stream);
+      if (e != cudaSuccess) return cuda_fail(l, e, "step kernel launch");
+      if (!periodic) {
+        if (fused) {  // the x_1-face-only nodes lead the list and are done
+          rest.sites = b.sites + l->nb_xface;
+          rest.nsites = b.nsites - l->nb_xface;
+          if (rest.roff) rest.roff += l->nb_xface;
+        }
+        e = launch_boundary(d, l->p.bc, dev, rest, l->stream);
+        if (e != cudaSuccess) return cuda_fail(l, e, "boundary kernel launch");
       }
-      e = launch_boundary(d, l->p.bc, dev, rest, l->stream);
-      if (e != cudaSuccess) return cuda_fail(l, e, "boundary kernel launch");
     }
     l->cur ^= 1;
     l->step += 1;

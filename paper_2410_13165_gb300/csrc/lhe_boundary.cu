@@ -198,7 +198,8 @@ __global__ void __launch_bounds__(128) k_jet_records(const BoundaryArgs a, const
         val -= dt * dt * dt / 16.0 * wp * ccht + dt * dt * dt / 24.0 * wp * j[J.i3[0]] + dt * dt * dt / 8.0 * wm * cgtt;
       }
     }
-    rec[r0 + ju++] = val;
+    rec[a.rmap ? a.rmap[r0 + ju] : r0 + ju] = val;  // node-major, or in the order of the dense entries
+    ++ju;
   }
 }
 

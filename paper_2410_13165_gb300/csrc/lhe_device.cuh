@@ -99,28 +99,16 @@ __host__ __device__ constexpr int ceil_log2(int q) {
 // the Q-1 additions of the moment sum (and the conversion) off the FP64 pipe.
 // Subnormal terms are placed as if their exponent were 0 instead of 1 (an error below 2^-1022 in
 // absolute value); any NaN or infinite term makes the result NaN.
-// The largest exponent and the integer total are each formed in NA independent partial chains
-// (term k in chain k mod NA), combined at the end: integer max and two's-complement addition are
-// associative, so the result does not depend on NA, while the dependent chain per node is NA times
-// shorter (the single chain of the Q additions stalled the large lattices on its latency).
 template <int Q, int P2, class Get>
 __device__ __forceinline__ double fixed_moment_sum_impl(Get f) {
   constexpr int G = 10 - ceil_log2(Q);
   static_assert(G >= 3, "too many terms for a 64-bit accumulator");
-  constexpr int NA = Q >= 8 ? 4 : 1;
-  unsigned em[NA];  // largest exponent field, in place (bits 20..30 of the high word)
+  unsigned emf = 0u;  // largest exponent field, in place (bits 20..30 of the high word)
 #pragma unroll
-  for (int j = 0; j < NA; ++j) em[j] = 0u;
-#pragma unroll
-  for (int k = 0; k < Q; ++k) em[k % NA] = max(em[k % NA], (unsigned)__double2hiint(f(k)) & 0x7FF00000u);
-  unsigned emf = em[0];
-#pragma unroll
-  for (int j = 1; j < NA; ++j) emf = max(emf, em[j]);
+  for (int k = 0; k < Q; ++k) emf = max(emf, (unsigned)__double2hiint(f(k)) & 0x7FF00000u);
   if (emf == 0x7FF00000u) return __longlong_as_double(0x7FF8000000000000ll);
   emf = max(emf, 0x00100000u);
-  long long part[NA];
-#pragma unroll
-  for (int j = 0; j < NA; ++j) part[j] = 0;
+  long long acc = 0;
 #pragma unroll
   for (int k = 0; k < Q; ++k) {
     const double fk = f(k);
@@ -135,11 +123,8 @@ __device__ __forceinline__ double fixed_moment_sum_impl(Get f) {
     else if (sh < 64u) v = (m + (1ull << (sh - 1))) >> sh;
     else v = 0ull;
     const long long sg = (long long)((int)hi >> 31);  // 0 or -1
-    part[k % NA] += ((long long)v ^ sg) - sg;
+    acc += ((long long)v ^ sg) - sg;
   }
-  long long acc = part[0];
-#pragma unroll
-  for (int j = 1; j < NA; ++j) acc += part[j];
   if (acc == 0) return 0.0;
   const unsigned long long sbit = acc < 0 ? 0x8000000000000000ull : 0ull;
   unsigned long long a = acc < 0 ? (unsigned long long)(-acc) : (unsigned long long)acc;

@@ -108,6 +108,7 @@ struct BoundaryArgs {
   // (half-way, Eq. (bun2) without -f*_kbar); rec == nullptr: data from the exact-solution family.
   const int32_t *roff;
   const double *rec;
+  const int32_t *rmap = nullptr;  // k_jet_records: the position of each record (else node-major)
   double rec_scale = 1.0;  // factor on every record (a separable solution's time factor)
   const double *Rfield;    // per-site source R(x) of the step, or nullptr for the constant R
   const void *src;
@@ -134,22 +135,10 @@ struct BoundaryArgs {
   double a[kMaxModes];
   double kappa[kMaxModes * kMaxD];
   double theta[kMaxModes];
-  // face rows with the family's data in separable form (k_step_face): the unknown population's data
-  // is P + lt_k + sum_m (A_m cos psi_m + B_m sin psi_m), psi_m = theta_m - kappa_m . u t_eval (ph_c, ph_s),
+  // the family's data in separable form (k_bdata_family): the unknown population's data is
+  // P + lt_k + sum_m (A_m cos psi_m + B_m sin psi_m), psi_m = theta_m - kappa_m . u t_eval (ph_c, ph_s),
   // lt_k the part linear in t_eval (one value per link and step)
   double lt[kMaxQ];
-};
-
-// A row of a Dirichlet box (all x_1 at fixed x_2..x_d) with some x_2..x_d on a face: its nodes are
-// boundary nodes, stepped in row order by k_step_face (FP64 forward).
-struct FaceRow {
-  uint64_t mask;   // links unknown at every node of the row (pull source outside the box in x_2..x_d)
-  int32_t row;     // row index: the node x_1 = 0 is site row * n_1
-  int32_t bmid;    // position in the boundary-node list of the node x_1 = 1 (the row's middle nodes
-                   // follow it in order); blo / bhi: the nodes x_1 = 0 and x_1 = n_1 - 1
-  int32_t blo, bhi;
-  int32_t slot;    // unknown-link slots of the rows before this one (sum of their popcount(mask))
-  int32_t pad;
 };
 
 struct InitArgs {
@@ -203,17 +192,21 @@ cudaError_t launch_sp_jets(int d, const SineProductArgs &a, const double *pts, i
 cudaError_t launch_sp_source(const SineProductArgs &a, const Geom &g, double *R0, cudaStream_t st);
 cudaError_t launch_scale_field(const double *in, double scale, int64_t n, double *out, int sms, cudaStream_t st);
 cudaError_t launch_step_box_fp64(int d, int kind, const StepArgs &a, const BoundaryArgs &b, double *xb, int64_t nrows,
-                                 const double *xsep, cudaStream_t st);
-// Separable coefficients of the family's data at the x_1-face nodes of the interior rows (xsep != nullptr
-// in launch_step_box_fp64 selects them).
-cudaError_t launch_xface_sep(int d, int kind, const BoundaryArgs &b, int64_t nrows, double *xsep, cudaStream_t st);
+                                 cudaStream_t st);
 cudaError_t launch_adjoint_boundary(int d, int kind, bool dev, const BoundaryArgs &a, cudaStream_t st);
-// Face rows (FP64 forward): data from the records of jets (b.rec, b.roff over the whole node list)
-// or, sep != nullptr, from the family's separable coefficients (k_face_sep).
-cudaError_t launch_step_face_fp64(int d, int kind, const StepArgs &a, const BoundaryArgs &b, const FaceRow *rows,
-                                  int64_t nrows, int32_t nslots, const double *sep, cudaStream_t st);
-cudaError_t launch_face_sep(int d, int kind, const BoundaryArgs &b, const FaceRow *rows, int64_t nrows, int32_t nslots,
-                            double *sep, cudaStream_t st);
+// FP64 step of a whole Dirichlet box: each unknown population k of node x is read from bdata[k S + x],
+// which launch_bdata_step fills for the step from the entries ent[e] = (k << 32) | x (sorted by k then
+// x): records in the order of the entries (times b.rec_scale) or, rec = false, the family's separable
+// coefficients (1 + 2M per entry, formed once per data set by family_sep); half-way minus f*_kbar(x)
+// of b.src.
+// The entries of links through a face of x_2..x_d are kept in the dense array; those of links through an
+// x_1 face only, at the row ends, after it (Q S + (2 row + h) (2d - 1) + j); dst[e] / opp[e]: each entry's
+// place there and the index of f*_kbar at its node (half-way).
+cudaError_t launch_step_box_dense(int d, const StepArgs &a, const double *bdata, cudaStream_t st);
+cudaError_t launch_bdata_step(int kind, bool rec, const BoundaryArgs &b, const long long *ent, const long long *dst,
+                              const long long *opp, int64_t nent, const double *data, double *bdata, cudaStream_t st);
+cudaError_t launch_family_sep(int d, int kind, const BoundaryArgs &b, const long long *ent, int64_t nent, double *sep,
+                              cudaStream_t st);
 cudaError_t launch_stability(int d, const double *omega_dev, int64_t npoints, int32_t nxi, double s,
                              unsigned long long *rho_bits_dev, cudaStream_t st);
 cudaError_t launch_init(int d, bool dev, const InitArgs &a, cudaStream_t st);
@@ -266,14 +259,18 @@ struct lhe_lbm {
   int64_t nb_xface = 0;         // leading entries of bsites on the x_1 faces only (other coordinates
                                 // interior): the FP64 forward step treats them in the row kernel
   double *xface = nullptr;      // their boundary data per step (2 (2d - 1) doubles per interior row)
-  // FP64 forward, d >= 2: the remaining boundary nodes as whole rows (k_step_face) unless
-  // LHE_FLAG_NO_FACE_ROWS; fsep: separable coefficients of the family's data on those rows
-  lhe::FaceRow *frows = nullptr;
-  int64_t nfrows = 0;
-  int32_t nfslots = 0;
+  // FP64 forward (unless LHE_FLAG_NODE_BOUNDARY): the boundary data of the step as a dense array
+  // shaped like the populations (set at the unknown entries only), and the separable coefficients of
+  // the family's data per record (1 + 2M doubles)
+  double *bdata = nullptr;
+  long long *bent = nullptr;    // its entries, (k << 32) | x: links through a face of x_2..x_d sorted by k then
+                                // x, then those through an x_1 face only sorted by x then k
+  long long *bdst = nullptr;    // each entry's place in bdata (the row-end part follows the Q S dense part)
+  long long *bopp = nullptr;    // kbar S + x of each entry (half-way)
+  int32_t *bmap = nullptr;      // the entry of each record (node-major index -> entry): records of jets and
+                                // of the manufactured solution are formed in the order of the entries
   double *fsep = nullptr;
   size_t fsep_len = 0;
-  bool fsep_ready = false;
   bool have_wave = false;
   lhe_wave wave{};
   // boundary data as jets (lhe_lbm_set_boundary_jet), one step at a time

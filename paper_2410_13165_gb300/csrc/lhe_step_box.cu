@@ -11,64 +11,6 @@ namespace {
 constexpr int kModeGeneral = 0, kModeS2 = 1;  // collision forms, as in lhe_step_fp64.cu
 }  // namespace
 
-// The family's data for unknown link k at a node, separated in time: P at p[0], A_m at p[(1 + 2m) st],
-// B_m at p[(2 + 2m) st]; G = b + g.x, sn/cs = sin/cos(kappa_m . x). Full-way (Eq. (bun1), tabulated):
-// omega_k [h - C_k - sum_m T_mk cos xi_m] with h = G + (R - g.u) t + sum_m a_m sin xi_m; half-way
-// (Eq. (bun2) without -f*_kbar): wp_k lin + K_k + sum_m (U_mk sin xi_m + V_mk cos xi_m), lin = G + (R - g.u) t;
-// xi_m = kappa_m . x + psi_m, so sin xi = sin(k.x) cos psi + cos(k.x) sin psi, cos xi = cos(k.x) cos psi -
-// sin(k.x) sin psi.
-template <int D, int KIND>
-__device__ __forceinline__ void family_sep_coefs(const BoundaryArgs &b, int k, double G, const double *sn,
-                                                 const double *cs, double *p, int st) {
-  constexpr int Q = Lattice<D>::Q;
-  const int M = b.nmodes;
-  const double *coef = b.table;                        // [m][k][2]
-  const double *kconst = b.table + (size_t)2 * M * Q;  // [k][2]
-  if (KIND == 1) {
-    const double w = b.omega[k];
-    p[0] = w * (G - kconst[2 * k]);
-    for (int m = 0; m < M; ++m) {
-      const double T = coef[2 * (m * Q + k)];
-      p[(1 + 2 * m) * st] = w * (b.a[m] * sn[m] - T * cs[m]);
-      p[(2 + 2 * m) * st] = w * (b.a[m] * cs[m] + T * sn[m]);
-    }
-  } else {
-    p[0] = fma(kconst[2 * k], G, kconst[2 * k + 1]);
-    for (int m = 0; m < M; ++m) {
-      const double U = coef[2 * (m * Q + k)], V = coef[2 * (m * Q + k) + 1];
-      p[(1 + 2 * m) * st] = U * sn[m] + V * cs[m];
-      p[(2 + 2 * m) * st] = U * cs[m] - V * sn[m];
-    }
-  }
-}
-
-// G = b + g.x and sin/cos(kappa_m . x) at node x.
-template <int D>
-__device__ __forceinline__ double family_node_phases(const BoundaryArgs &b, const int (&x)[D], double *sn, double *cs) {
-  double G = b.b;
-#pragma unroll
-  for (int i = 0; i < D; ++i) G = fma(b.gl[i], b.x0[i] + (double)x[i] * b.dx, G);
-  for (int m = 0; m < b.nmodes; ++m) {
-    double ph = 0.0;
-#pragma unroll
-    for (int i = 0; i < D; ++i) ph = fma(b.kappa[m * kMaxD + i], b.x0[i] + (double)x[i] * b.dx, ph);
-    sincos(ph, &sn[m], &cs[m]);
-  }
-  return G;
-}
-
-// The family's data from separable coefficients p (stride st) at this step: P + lt_k + sum_m (A_m cos psi_m
-// + B_m sin psi_m).
-__device__ __forceinline__ double family_sep_value(const BoundaryArgs &b, int k, const double *p, int st) {
-  double v = __ldg(p) + b.lt[k];
-  for (int m = 0; m < b.nmodes; ++m) {
-    v = fma(__ldg(p + (1 + 2 * m) * st), b.ph_c[m], v);
-    v = fma(__ldg(p + (2 + 2 * m) * st), b.ph_s[m], v);
-  }
-  return v;
-}
-
-
 // The unknown populations of the x_1-face nodes of a Dirichlet box (those whose other coordinates
 // are interior), for k_step_box: for interior row r (x_2..x_D interior) and side h (0: x_1 = 0, 1:
 // x_1 = n_1 - 1), the 2D - 1 unknown links (e_k,1 = +1 on the low side, -1 on the high side) at
@@ -77,8 +19,7 @@ __device__ __forceinline__ double family_sep_value(const BoundaryArgs &b, int k,
 // list, low face then high face, each in row order), and for the half-way scheme minus f*_kbar at the
 // node (the state at the start of the step).
 template <int D, int KIND>
-__global__ void __launch_bounds__(128) k_xface_data(const BoundaryArgs b, double *__restrict__ xb, int64_t nrows,
-                                                    const double *__restrict__ xsep) {
+__global__ void __launch_bounds__(128) k_xface_data(const BoundaryArgs b, double *__restrict__ xb, int64_t nrows) {
   constexpr Lattice<D> L{};
   constexpr int Q = Lattice<D>::Q;
   constexpr int J = 2 * D - 1;
@@ -109,17 +50,6 @@ __global__ void __launch_bounds__(128) k_xface_data(const BoundaryArgs b, double
       if (L.e[k][0] == sgn) {
         const int j = xface_link<D>(k, sgn);
         const double v = b.rec_scale * __ldg(rec + j);
-        xb[t * J + j] = KIND == 1 ? v : v - bnode_fkb<D, false>(b, k, site);
-      }
-    return;
-  }
-  if (xsep) {  // the family's data from separable coefficients (with face rows, see k_xface_sep)
-    const int C = 1 + 2 * b.nmodes;
-#pragma unroll
-    for (int k = 0; k < Q; ++k)
-      if (L.e[k][0] == sgn) {
-        const int j = xface_link<D>(k, sgn);
-        const double v = family_sep_value(b, k, xsep + (t * J + j) * C, 1);
         xb[t * J + j] = KIND == 1 ? v : v - bnode_fkb<D, false>(b, k, site);
       }
     return;
@@ -176,167 +106,180 @@ __global__ void __launch_bounds__(LHE_STEP_THREADS) k_step_box(const StepArgs a,
   }
 }
 
-// ------------------------------------------------------------------------------ face rows
-// The boundary nodes off the x_1 faces lie on whole rows (fixed x_2..x_d with some of them on a
-// face). Their unknown populations at the middle nodes of a row are the same links for the whole row
-// (FaceRow::mask), so a row kernel like k_step_box takes them in the same load instructions as the
-// pulled ones, reading coalesced data; the two end nodes add the links of their x_1 face. This
-// replaces the boundary-node kernel for these nodes in the FP64 forward step. Data:
-//   records (jets, the manufactured solution): per node, in the order of k over its unknown links,
-//     times rec_scale (the values of the boundary-node kernel, bit for bit);
-//   the exact-solution family: separable coefficients formed once per data set (k_face_sep):
-//     data_k(x, t) = P + lt_k + sum_m (A_m cos psi_m + B_m sin psi_m), psi_m = theta_m - kappa_m . u t,
-//     with P, A_m, B_m per (node, unknown link) and lt_k = q_k t per link and step.
-// Half-way: minus f*_kbar at the node (the state at the start of the step), as in k_boundary.
-// Layout of the coefficients, C = 1 + 2M per (node, link): row slot j of face row r at
-// ((slot_r + j) C + c) n_1 + x_1 (coalesced over x_1); the end nodes' x_1-face links at
-// E + ((2 r + h) J + jx) C + c, E = nslots C n_1, J = 2d - 1, h = 0 (x_1 = 0) or 1, jx = xface_link.
+// ------------------------------------------------------------------------------ dense boundary data
+// The whole box in one row kernel. The boundary data of a step are kept in an array shaped like the
+// populations, bdata[k S + x], set only where population k of node x is unknown (its pull source
+// x - e_k lies outside the box): the step kernel then chooses, per link and lane, between that entry
+// and the pulled population by address arithmetic alone, so every load of a lane is independent and
+// coalesced, boundary nodes or not. The producers below fill the entries from the records of jets or
+// the manufactured solution (copied in the order of k over each node's unknown links, bit for bit the
+// values of the boundary-node kernel) or from the exact-solution family (its data separated in time,
+// formed once per data set).
 
+// Lattice coordinates of `site` (x_1 fastest).
 template <int D>
-__host__ __device__ constexpr uint64_t xface_mask(int sgn) {
-  constexpr Lattice<D> L{};
-  uint64_t m = 0;
-  for (int k = 0; k < Lattice<D>::Q; ++k)
-    if (L.e[k][0] == sgn) m |= 1ull << k;
-  return m;
-}
-
-// Coefficient pointer and stride of unknown link k at node x_1 of face row r (see the layout above).
-template <int D>
-__device__ __forceinline__ const double *face_coef(const FaceRow &fr, uint32_t r, int x1, int face1, int k, int C,
-                                                   int n1, int32_t nslots, const double *sep, int &cs) {
-  if ((fr.mask >> k) & 1ull) {
-    const int j = __popcll(fr.mask & ((1ull << k) - 1ull));
-    cs = n1;
-    return sep + ((int64_t)(fr.slot + j) * C) * n1 + x1;
-  }
-  constexpr int J = 2 * D - 1;
-  const int h = face1 > 0 ? 0 : 1;
-  cs = 1;
-  return sep + (int64_t)nslots * C * n1 + ((int64_t)(2 * r + h) * J + xface_link<D>(k, face1)) * C;
-}
-
-// Separable coefficients of the family's boundary data on the face rows (once per data set).
-template <int D, int KIND>
-__global__ void __launch_bounds__(128) k_face_sep(const BoundaryArgs b, const FaceRow *__restrict__ rows, int64_t nwork,
-                                                  int32_t nslots, double *__restrict__ sep) {
-  constexpr Lattice<D> L{};
-  constexpr int Q = Lattice<D>::Q;
-  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (t >= nwork) return;
-  const int n1 = b.g.n[0];
-  const uint32_t r = b.g.dv[0].div((uint32_t)t);
-  const int x1 = (int)((uint32_t)t - r * (uint32_t)n1);
-  const FaceRow fr = rows[r];
-  int x[D];
-  x[0] = x1;
-  {
-    uint32_t q = (uint32_t)fr.row;
+__device__ __forceinline__ void site_coords(const Geom &g, int32_t site, int (&x)[D]) {
+  uint32_t r = (uint32_t)site;
 #pragma unroll
-    for (int i = 1; i < D; ++i) {
-      if (i == D - 1) {
-        x[i] = (int)q;
-      } else {
-        const uint32_t q2 = b.g.dv[i].div(q);
-        x[i] = (int)(q - q2 * (uint32_t)b.g.n[i]);
-        q = q2;
-      }
-    }
-  }
-  const int face1 = x1 == 0 ? 1 : (x1 == n1 - 1 ? -1 : 0);
-  const int C = 1 + 2 * b.nmodes;
-  double sn[kMaxModes], cs[kMaxModes];
-  const double G = family_node_phases<D>(b, x, sn, cs);
-#pragma unroll
-  for (int k = 0; k < Q; ++k) {
-    const bool row_link = (fr.mask >> k) & 1ull;
-    if (!row_link && !(face1 != 0 && L.e[k][0] == face1)) continue;
-    int st = 0;
-    double *p = const_cast<double *>(face_coef<D>(fr, r, x1, face1, k, C, n1, nslots, sep, st));
-    family_sep_coefs<D, KIND>(b, k, G, sn, cs, p, st);
-  }
-}
-
-// Separable coefficients of the family's data for the x_1-face nodes of the interior rows (k_xface_data),
-// at xsep + ((2 r + h) J + j) C: row r, side h, link j = xface_link (once per data set).
-template <int D, int KIND>
-__global__ void __launch_bounds__(128) k_xface_sep(const BoundaryArgs b, int64_t nrows, double *__restrict__ xsep) {
-  constexpr Lattice<D> L{};
-  constexpr int Q = Lattice<D>::Q;
-  constexpr int J = 2 * D - 1;
-  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (t >= 2 * nrows) return;
-  const int h = (int)(t & 1);
-  uint32_t r = (uint32_t)(t >> 1);
-  int x[D];
-  x[0] = h ? b.g.n[0] - 1 : 0;
-#pragma unroll
-  for (int i = 1; i < D; ++i) {
+  for (int i = 0; i < D; ++i) {
     if (i == D - 1) {
-      x[i] = (int)r + 1;
+      x[i] = (int)r;
     } else {
-      const uint32_t q = b.g.dvi[i].div(r);
-      x[i] = (int)(r - q * (uint32_t)(b.g.n[i] - 2)) + 1;
+      const uint32_t q = g.dv[i].div(r);
+      x[i] = (int)(r - q * (uint32_t)g.n[i]);
       r = q;
     }
   }
-  const int sgn = h ? -1 : 1, C = 1 + 2 * b.nmodes;
-  double sn[kMaxModes], cs[kMaxModes];
-  const double G = family_node_phases<D>(b, x, sn, cs);
-#pragma unroll
-  for (int k = 0; k < Q; ++k)
-    if (L.e[k][0] == sgn) family_sep_coefs<D, KIND>(b, k, G, sn, cs, xsep + (t * J + xface_link<D>(k, sgn)) * C, 1);
 }
 
-// FP64 forward step of the face rows (one lane per node, rows of n_1 lanes).
-template <int D, int KIND, int MODE, bool SEP>
-__global__ void __launch_bounds__(LHE_STEP_THREADS) k_step_face(const StepArgs a, const BoundaryArgs b,
-                                                                const FaceRow *__restrict__ rows, int32_t nslots,
-                                                                const double *__restrict__ sep) {
+// The family's data for unknown link k at a node, separated in time: P at p[0], A_m at p[(1 + 2m) st],
+// B_m at p[(2 + 2m) st]; G = b + g.x, sn/cs = sin/cos(kappa_m . x). Full-way (Eq. (bun1), tabulated):
+// omega_k [h - C_k - sum_m T_mk cos xi_m] with h = G + (R - g.u) t + sum_m a_m sin xi_m; half-way
+// (Eq. (bun2) without -f*_kbar): wp_k lin + K_k + sum_m (U_mk sin xi_m + V_mk cos xi_m), lin = G + (R - g.u) t;
+// xi_m = kappa_m . x + psi_m, so sin xi = sin(k.x) cos psi + cos(k.x) sin psi, cos xi = cos(k.x) cos psi -
+// sin(k.x) sin psi.
+template <int D, int KIND>
+__device__ __forceinline__ void family_sep_coefs(const BoundaryArgs &b, int k, double G, const double *sn,
+                                                 const double *cs, double *p, int st) {
+  constexpr int Q = Lattice<D>::Q;
+  const int M = b.nmodes;
+  const double *coef = b.table;                        // [m][k][2]
+  const double *kconst = b.table + (size_t)2 * M * Q;  // [k][2]
+  if (KIND == 1) {
+    const double w = b.omega[k];
+    p[0] = w * (G - kconst[2 * k]);
+    for (int m = 0; m < M; ++m) {
+      const double T = coef[2 * (m * Q + k)];
+      p[(1 + 2 * m) * st] = w * (b.a[m] * sn[m] - T * cs[m]);
+      p[(2 + 2 * m) * st] = w * (b.a[m] * cs[m] + T * sn[m]);
+    }
+  } else {
+    p[0] = fma(kconst[2 * k], G, kconst[2 * k + 1]);
+    for (int m = 0; m < M; ++m) {
+      const double U = coef[2 * (m * Q + k)], V = coef[2 * (m * Q + k) + 1];
+      p[(1 + 2 * m) * st] = U * sn[m] + V * cs[m];
+      p[(2 + 2 * m) * st] = U * cs[m] - V * sn[m];
+    }
+  }
+}
+
+// The family's data from separable coefficients p (stride st) at this step: P + lt_k + sum_m (A_m cos psi_m
+// + B_m sin psi_m).
+__device__ __forceinline__ double family_sep_value(const BoundaryArgs &b, int k, const double *p, int st) {
+  double v = __ldg(p) + b.lt[k];
+  for (int m = 0; m < b.nmodes; ++m) {
+    v = fma(__ldg(p + (1 + 2 * m) * st), b.ph_c[m], v);
+    v = fma(__ldg(p + (2 + 2 * m) * st), b.ph_s[m], v);
+  }
+  return v;
+}
+
+// The entries that a step sets, one per (unknown link k, boundary node x), given as ent[e] = (k << 32) | x:
+// first those whose pull source leaves the box through a face of x_2..x_d ("row links": for the whole
+// row the same links), sorted by k and then by x, kept in the dense array bdata[k S + x], where they form
+// runs of at least n_1 nodes; then the links through an x_1 face only, at the two end nodes of each row,
+// kept after it at Q S + (2 row + h) J + jx (h = 0 at x_1 = 0, 1 at x_1 = n_1 - 1; J = 2d - 1;
+// jx = xface_link), compact per row end. Both producers' writes and the step kernel's reads are then contiguous.
+
+// Links with e_k,i = sgn (bit k): those unknown at a node on the low (sgn = 1) or high (-1) face of axis i.
+template <int D>
+__host__ __device__ constexpr uint64_t face_links(int i, int sgn) {
+  constexpr Lattice<D> L{};
+  uint64_t m = 0;
+  for (int k = 0; k < Lattice<D>::Q; ++k)
+    if (L.e[k][i] == sgn) m |= 1ull << k;
+  return m;
+}
+
+// The links of node x that leave the box through a face of x_2..x_d (bit k).
+template <int D>
+__device__ __forceinline__ uint64_t row_links_out(const Geom &g, const int (&x)[D]) {
+  uint64_t m = 0;
+#pragma unroll
+  for (int i = 1; i < D; ++i) {
+    if (x[i] == 0) m |= face_links<D>(i, 1);
+    if (x[i] == g.n[i] - 1) m |= face_links<D>(i, -1);
+  }
+  return m;
+}
+
+// Separable coefficients of the family's data per entry, sep[e C + c], C = 1 + 2M. Once per data set.
+template <int D, int KIND>
+__global__ void __launch_bounds__(128) k_family_sep(const BoundaryArgs b, const long long *__restrict__ ent,
+                                                    int64_t nent, double *__restrict__ sep) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= nent) return;
+  const long long tg = ent[e];
+  const int k = (int)(tg >> 32);
+  const int32_t site = (int32_t)(tg & 0xffffffffll);
+  int x[D];
+  site_coords<D>(b.g, site, x);
+  double G = b.b;  // b + g.x
+#pragma unroll
+  for (int i = 0; i < D; ++i) G = fma(b.gl[i], b.x0[i] + (double)x[i] * b.dx, G);
+  double sn[kMaxModes], cs[kMaxModes];  // sin and cos of kappa_m . x
+  for (int m = 0; m < b.nmodes; ++m) {
+    double ph = 0.0;
+#pragma unroll
+    for (int i = 0; i < D; ++i) ph = fma(b.kappa[m * kMaxD + i], b.x0[i] + (double)x[i] * b.dx, ph);
+    sincos(ph, &sn[m], &cs[m]);
+  }
+  family_sep_coefs<D, KIND>(b, k, G, sn, cs, sep + e * (1 + 2 * b.nmodes), 1);
+}
+
+// The unknown populations of this step into the dense array, one thread per entry (k, x): the records
+// (formed in the order of the entries) times rec_scale, or the family's data from its separable
+// coefficients (lt, ph_c, ph_s of the step in b); half-way minus f*_kbar(x) of the state at the start
+// of the step (a.src). The same operations, in the same order, as the boundary-node kernel.
+// dst[e] is the entry's place in the dense array (k S + x) or, for the row-end entries, after it
+// (Q S + (2 row + h) J + jx); opp[e] = kbar S + x, the population subtracted by the half-way scheme.
+template <int KIND, bool REC>
+__global__ void __launch_bounds__(256) k_bdata_step(const BoundaryArgs b, const long long *__restrict__ ent,
+                                                    const long long *__restrict__ dst, const long long *__restrict__ opp,
+                                                    int64_t nent, const double *__restrict__ data,
+                                                    double *__restrict__ bdata) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= nent) return;
+  double v = REC ? b.rec_scale * __ldg(data + e)
+                 : family_sep_value(b, (int)(__ldg(ent + e) >> 32), data + e * (1 + 2 * b.nmodes), 1);
+  if (KIND == 2) v = v - __ldg(static_cast<const double *>(b.src) + __ldg(opp + e));
+  bdata[__ldg(dst + e)] = v;
+}
+
+// FP64 step of every node of a Dirichlet box (whole rows, x_1 fastest): each population is the pulled
+// one or, when unknown, the entry of the dense array that k_bdata_step set for this step; then the
+// collision of the bulk. No arithmetic per link: on GB300 an FP64 operation per link costs as much as
+// the collision (the FP64 pipe retires ~2 per clock per SM).
+template <int D, int MODE>
+__global__ void __launch_bounds__(LHE_STEP_THREADS) k_step_box_dense(const StepArgs a, const double *__restrict__ bdata) {
   constexpr Lattice<D> L{};
   constexpr int Q = Lattice<D>::Q;
-  constexpr uint64_t xlo = xface_mask<D>(1), xhi = xface_mask<D>(-1);
   pdl_trigger();
   pdl_wait();
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= a.nwork) return;
-  const int n1 = a.g.n[0];
-  const uint32_t r = a.g.dv[0].div((uint32_t)t);
-  const int x1 = (int)((uint32_t)t - r * (uint32_t)n1);
-  const FaceRow fr = rows[r];
-  const int32_t site = fr.row * n1 + x1;
-  const int face1 = x1 == 0 ? 1 : (x1 == n1 - 1 ? -1 : 0);
-  const uint64_t nmask = fr.mask | (face1 > 0 ? xlo : (face1 < 0 ? xhi : 0ull));  // this node's unknown links
+  constexpr int J = 2 * D - 1;
+  int x[D];
+  const int32_t site = decode_site<D, false>(a.g, t, x);
+  const int side1 = x[0] == 0 ? 1 : (x[0] == a.g.n[0] - 1 ? -1 : 0);
+  // this row end's x_1-face entries, after the dense part
+  const double *xrow = bdata + (int64_t)Q * a.g.S + ((int64_t)2 * a.g.dv[0].div((uint32_t)t) + (side1 < 0 ? 1 : 0)) * J;
   const double *__restrict__ src = static_cast<const double *>(a.src);
   double *__restrict__ dst = static_cast<double *>(a.dst);
   const int64_t S = a.g.S;
   const double Rs = a.Rfield ? __ldg(a.Rfield + site) : 0.0;
-  const double *rec = nullptr;
-  if (!SEP) rec = b.rec + b.roff[face1 > 0 ? fr.blo : (face1 < 0 ? fr.bhi : fr.bmid + x1 - 1)];
-  const int C = 1 + 2 * b.nmodes;
   double f[Q];
+  const uint64_t row_out = row_links_out<D>(a.g, x);
+  const uint64_t x_out = side1 > 0 ? face_links<D>(0, 1) : (side1 < 0 ? face_links<D>(0, -1) : 0ull);
 #pragma unroll
   for (int k = 0; k < Q; ++k) {
-    const bool unknown = (nmask >> k) & 1ull;
+    const bool row_unknown = (row_out >> k) & 1ull;
+    const bool x_unknown = (x_out >> k) & 1ull;
+    const int jx = L.e[k][0] == 1 ? xface_link<D>(k, 1) : xface_link<D>(k, -1);
     int32_t o = site;  // pull source x - e_k (inside the box when the link is known)
 #pragma unroll
     for (int i = 0; i < D; ++i) o -= L.e[k][i] * a.g.stride[i];
-    if (!SEP) {
-      const int j = __popcll(nmask & ((1ull << k) - 1ull));
-      const double v = __ldg(unknown ? rec + j : src + k * S + o);
-      if (unknown) {
-        const double bv = b.rec_scale * v;
-        f[k] = KIND == 1 ? bv : bv - bnode_fkb<D, false>(b, k, site);
-      } else {
-        f[k] = v;
-      }
-    } else if (unknown) {
-      int cs = 0;
-      const double v = family_sep_value(b, k, face_coef<D>(fr, r, x1, face1, k, C, n1, nslots, sep, cs), cs);
-      f[k] = KIND == 1 ? v : v - bnode_fkb<D, false>(b, k, site);
-    } else {
-      f[k] = __ldg(src + k * S + o);
-    }
+    f[k] = __ldg(row_unknown ? bdata + k * S + site : (x_unknown ? xrow + jx : src + k * S + o));
   }
   const double psi = MODE == kModeS2 ? fixed_moment_sum<Q, 1>(f) + (a.Rfield ? a.dt * Rs : a.dtR)
                                      : fma(a.sig, fixed_moment_sum<Q, 0>(f), a.Rfield ? a.rho_dt * Rs : a.rho_dtR);
@@ -348,84 +291,70 @@ __global__ void __launch_bounds__(LHE_STEP_THREADS) k_step_face(const StepArgs a
 }
 
 template <int D>
-static cudaError_t step_face_d(int kind, const StepArgs &a, const BoundaryArgs &b, const FaceRow *rows, int32_t nslots,
-                               const double *sep, cudaStream_t st) {
-  if (a.nwork <= 0) return cudaSuccess;
+static cudaError_t step_box_dense_d(const StepArgs &a, const double *bdata, cudaStream_t st) {
   const int threads = LHE_STEP_THREADS;
   const unsigned blocks = (unsigned)((a.nwork + threads - 1) / threads);
-  const bool s2 = a.s == 2.0, fw = kind == 1;
-#define LHE_FACE(K, M, SP) launch_kernel(k_step_face<D, K, M, SP>, blocks, threads, 0, st, false, a, b, rows, nslots, sep)
-  if (sep) {
-    if (fw) return s2 ? LHE_FACE(1, kModeS2, true) : LHE_FACE(1, kModeGeneral, true);
-    return s2 ? LHE_FACE(2, kModeS2, true) : LHE_FACE(2, kModeGeneral, true);
-  }
-  if (fw) return s2 ? LHE_FACE(1, kModeS2, false) : LHE_FACE(1, kModeGeneral, false);
-  return s2 ? LHE_FACE(2, kModeS2, false) : LHE_FACE(2, kModeGeneral, false);
-#undef LHE_FACE
+  const bool pdl = a.pdl != 0;
+  if (a.s == 2.0) return launch_kernel(k_step_box_dense<D, kModeS2>, blocks, threads, 0, st, pdl, a, bdata);
+  return launch_kernel(k_step_box_dense<D, kModeGeneral>, blocks, threads, 0, st, pdl, a, bdata);
 }
 
-cudaError_t launch_step_face_fp64(int d, int kind, const StepArgs &a, const BoundaryArgs &b, const FaceRow *rows,
-                                  int64_t nrows, int32_t nslots, const double *sep, cudaStream_t st) {
+cudaError_t launch_step_box_dense(int d, const StepArgs &a, const double *bdata, cudaStream_t st) {
   StepArgs aa = a;
-  aa.nwork = nrows * a.g.n[0];
+  aa.nwork = a.g.S;
+  if (aa.nwork <= 0) return cudaSuccess;
   switch (d) {
-    case 2: return step_face_d<2>(kind, aa, b, rows, nslots, sep, st);
-    case 3: return step_face_d<3>(kind, aa, b, rows, nslots, sep, st);
-    case 4: return step_face_d<4>(kind, aa, b, rows, nslots, sep, st);
-    case 5: return step_face_d<5>(kind, aa, b, rows, nslots, sep, st);
+    case 1: return step_box_dense_d<1>(aa, bdata, st);
+    case 2: return step_box_dense_d<2>(aa, bdata, st);
+    case 3: return step_box_dense_d<3>(aa, bdata, st);
+    case 4: return step_box_dense_d<4>(aa, bdata, st);
+    case 5: return step_box_dense_d<5>(aa, bdata, st);
     default: return cudaErrorInvalidValue;
   }
 }
 
-cudaError_t launch_xface_sep(int d, int kind, const BoundaryArgs &b, int64_t nrows, double *xsep, cudaStream_t st) {
-  if (nrows <= 0) return cudaSuccess;
-  const unsigned blocks = (unsigned)((2 * nrows + 127) / 128);
-#define LHE_XSEP(DD)                                                              \
-  do {                                                                            \
-    if (kind == 1) k_xface_sep<DD, 1><<<blocks, 128, 0, st>>>(b, nrows, xsep);   \
-    else k_xface_sep<DD, 2><<<blocks, 128, 0, st>>>(b, nrows, xsep);             \
-  } while (0)
-  switch (d) {
-    case 1: LHE_XSEP(1); break;
-    case 2: LHE_XSEP(2); break;
-    case 3: LHE_XSEP(3); break;
-    case 4: LHE_XSEP(4); break;
-    case 5: LHE_XSEP(5); break;
-    default: return cudaErrorInvalidValue;
+cudaError_t launch_bdata_step(int kind, bool rec, const BoundaryArgs &b, const long long *ent, const long long *dst,
+                              const long long *opp, int64_t nent, const double *data, double *bdata, cudaStream_t st) {
+  if (nent <= 0) return cudaSuccess;
+  const unsigned blocks = (unsigned)((nent + 255) / 256);
+  if (kind == 1) {
+    if (rec) k_bdata_step<1, true><<<blocks, 256, 0, st>>>(b, ent, dst, opp, nent, data, bdata);
+    else k_bdata_step<1, false><<<blocks, 256, 0, st>>>(b, ent, dst, opp, nent, data, bdata);
+  } else {
+    if (rec) k_bdata_step<2, true><<<blocks, 256, 0, st>>>(b, ent, dst, opp, nent, data, bdata);
+    else k_bdata_step<2, false><<<blocks, 256, 0, st>>>(b, ent, dst, opp, nent, data, bdata);
   }
-#undef LHE_XSEP
   return cudaGetLastError();
 }
 
-cudaError_t launch_face_sep(int d, int kind, const BoundaryArgs &b, const FaceRow *rows, int64_t nrows, int32_t nslots,
-                            double *sep, cudaStream_t st) {
-  const int64_t nwork = nrows * b.g.n[0];
-  if (nwork <= 0) return cudaSuccess;
-  const unsigned blocks = (unsigned)((nwork + 127) / 128);
-#define LHE_SEP(DD)                                                                      \
-  do {                                                                                    \
-    if (kind == 1) k_face_sep<DD, 1><<<blocks, 128, 0, st>>>(b, rows, nwork, nslots, sep); \
-    else k_face_sep<DD, 2><<<blocks, 128, 0, st>>>(b, rows, nwork, nslots, sep);           \
-  } while (0)
+cudaError_t launch_family_sep(int d, int kind, const BoundaryArgs &b, const long long *ent, int64_t nent, double *sep,
+                              cudaStream_t st) {
+  if (nent <= 0) return cudaSuccess;
+  const unsigned blocks = (unsigned)((nent + 127) / 128);
+  const bool fw = kind == 1;
+#define LHE_FSEP(DD) \
+  (fw ? k_family_sep<DD, 1><<<blocks, 128, 0, st>>>(b, ent, nent, sep) : k_family_sep<DD, 2><<<blocks, 128, 0, st>>>(b, ent, nent, sep))
   switch (d) {
-    case 2: LHE_SEP(2); break;
-    case 3: LHE_SEP(3); break;
-    case 4: LHE_SEP(4); break;
-    case 5: LHE_SEP(5); break;
+    case 1: LHE_FSEP(1); break;
+    case 2: LHE_FSEP(2); break;
+    case 3: LHE_FSEP(3); break;
+    case 4: LHE_FSEP(4); break;
+    case 5: LHE_FSEP(5); break;
     default: return cudaErrorInvalidValue;
   }
-#undef LHE_SEP
+#undef LHE_FSEP
   return cudaGetLastError();
 }
+
 
 template <int D>
 static cudaError_t step_box_d(int kind, const StepArgs &a, const BoundaryArgs &b, double *xb, int64_t nrows,
-                              const double *xsep, cudaStream_t st) {
+                              cudaStream_t st) {
   if (a.nwork <= 0) return cudaSuccess;
   const unsigned dblocks = (unsigned)((2 * nrows + 127) / 128);
   cudaError_t e;
-  if (kind == 1) k_xface_data<D, 1><<<dblocks, 128, 0, st>>>(b, xb, nrows, xsep);
-  else k_xface_data<D, 2><<<dblocks, 128, 0, st>>>(b, xb, nrows, xsep);
+  if (kind == 1) k_xface_data<D, 1><<<dblocks, 128, 0, st>>>(b, xb, nrows);
+  else k_xface_data<D, 2><<<dblocks, 128, 0, st>>>(b, xb, nrows);
   if ((e = cudaGetLastError())) return e;
   const int threads = LHE_STEP_THREADS;
   const unsigned blocks = (unsigned)((a.nwork + threads - 1) / threads);
@@ -435,13 +364,13 @@ static cudaError_t step_box_d(int kind, const StepArgs &a, const BoundaryArgs &b
 }
 
 cudaError_t launch_step_box_fp64(int d, int kind, const StepArgs &a, const BoundaryArgs &b, double *xb, int64_t nrows,
-                                 const double *xsep, cudaStream_t st) {
+                                 cudaStream_t st) {
   switch (d) {
-    case 1: return step_box_d<1>(kind, a, b, xb, nrows, xsep, st);
-    case 2: return step_box_d<2>(kind, a, b, xb, nrows, xsep, st);
-    case 3: return step_box_d<3>(kind, a, b, xb, nrows, xsep, st);
-    case 4: return step_box_d<4>(kind, a, b, xb, nrows, xsep, st);
-    case 5: return step_box_d<5>(kind, a, b, xb, nrows, xsep, st);
+    case 1: return step_box_d<1>(kind, a, b, xb, nrows, st);
+    case 2: return step_box_d<2>(kind, a, b, xb, nrows, st);
+    case 3: return step_box_d<3>(kind, a, b, xb, nrows, st);
+    case 4: return step_box_d<4>(kind, a, b, xb, nrows, st);
+    case 5: return step_box_d<5>(kind, a, b, xb, nrows, st);
     default: return cudaErrorInvalidValue;
   }
 }

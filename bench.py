@@ -364,9 +364,10 @@ def _run_ours(args, clk):
                             "note": "s = 2 collision, timed separately (50 steps)"}
     # the precision form at 128^3 (the precision workload's grid), where a step is ~0.1 ms and fixed
     # costs per launch weigh most: FP32 deviations vs FP64 in calls of one step and of 50 steps
-    forms["precision_128"] = precision_ratio_128(W, LBM, clk, ws)
-    # the differentiation workload (D3Q19 128^3, FP32 deviations, T = 1024 through torch.autograd)
-    forms["differentiation_128"] = differentiation_workload(clk)
+    if args.extra_forms:
+        forms["precision_128"] = precision_ratio_128(W, LBM, clk, ws)
+        # the differentiation workload (D3Q19 128^3, FP32 deviations, T = 1024 through torch.autograd)
+        forms["differentiation_128"] = differentiation_workload(clk)
     fp64 = forms["fp64"]
     kernel_src = os.path.join(ROOT, "paper_2410_13165_gb300", "csrc", "lhe_step_fp64.cu")
     traffic = profiled_traffic(kernel_src)
@@ -899,6 +900,8 @@ def main():
     ap.add_argument("--ref-n", type=int, default=128)
     ap.add_argument("--error-steps", type=int, default=2000)
     ap.add_argument("--oracle-steps", type=int, default=50)
+    ap.add_argument("--extra-forms", type=int, default=1,
+                    help="default line: also measure the precision form and the differentiation workload at 128^3")
     ap.add_argument("--workload", default="d3q19_256",
                     choices=["d3q19_256", "d4q33_dirichlet", "d5q51_fp32dev", "adjoint", "convergence",
                              "order_law", "examples", "stability_map", "fp32_floor"])

@@ -22,9 +22,10 @@
 namespace lhe {
 
 // Register caps for the large lattices: D4Q33 at 5 resident blocks per SM (96 registers, no spills)
-// and D5Q51 at 4 (128 registers instead of 146, 16 bytes spilled) keep more loads in flight per SM;
-// measured 71 -> 87 % and 66 -> 74 % of the HBM bandwidth (D4Q33 48^4, D5Q51 24^5). The FP64 kernel
-// is not capped: there the spills cost more than the occupancy gains (D5Q51 76 -> 66 %).
+// and D5Q51 at 4 (128 registers; 126 and no spills with its two-pass form below) keep more loads in
+// flight per SM; measured 71 -> 87 % and 66 -> 74 % of the HBM bandwidth (D4Q33 48^4, D5Q51 24^5), 76 %
+// for D5Q51 in two passes. The FP64 kernel is not capped: there the spills cost more than the occupancy
+// gains (D5Q51 76 -> 66 %).
 template <int D>
 constexpr int dev_min_blocks() { return D == 4 ? 5 : (D == 5 ? 4 : 1); }
 

@@ -368,6 +368,8 @@ def _run_ours(args, clk):
         forms["precision_128"] = precision_ratio_128(W, LBM, clk, ws)
         # the differentiation workload (D3Q19 128^3, FP32 deviations, T = 1024 through torch.autograd)
         forms["differentiation_128"] = differentiation_workload(clk)
+        # the Dirichlet box of Example 3 (D4Q33 64^4, full-way, order 4)
+        forms["dirichlet_d4q33_64"] = dirichlet_box_form(clk, ws)
     fp64 = forms["fp64"]
     kernel_src = os.path.join(ROOT, "paper_2410_13165_gb300", "csrc", "lhe_step_fp64.cu")
     traffic = profiled_traffic(kernel_src)
@@ -457,6 +459,33 @@ def precision_ratio_128(W, LBM, clk, ws, n=128):
         out["tau%g" % tau] = dict(ms, ratio_one_step_calls=ms["fp64"]["ms_one_step_calls"] / ms["fp32dev"]["ms_one_step_calls"],
                                   ratio_50_step_calls=ms["fp64"]["ms_50_step_calls"] / ms["fp32dev"]["ms_50_step_calls"])
     return out
+
+
+def dirichlet_box_form(clk, ws, n=64, steps=20):
+    """Example 3's box [-1, 1]^4 (n^4 nodes, D4Q33), phi = sin(pi sum_i (x_i - u_i t)), full-way order-4
+    boundaries, u = (0.05, 0.2, 0.08, 0.1), K = 3: time per step (boundary data included) and the fraction
+    of the roofline of an interior node (528 B per node and step)."""
+    import torch
+
+    from paper_2410_13165_gb300 import LBM
+    from paper_2410_13165_gb300 import workloads as W
+
+    u = (0.05, 0.2, 0.08, 0.1)
+    X = W.node_coords(4, n, -1.0, 2.0 / (n - 1))
+    arg = np.pi * X.sum(axis=0)
+    del X
+    phi0 = torch.from_numpy(np.sin(arg)).cuda()
+    grad = torch.from_numpy(np.repeat((np.pi * np.cos(arg))[None, :], 4, axis=0).ravel()).cuda()
+    del arg
+    sim = LBM(4, n, -1.0, 1.0, u=u, bc="fullway")
+    sim.init(phi0, grad)
+    del phi0, grad
+    sim.set_boundary_wave([1.0], [[np.pi] * 4], [0.0])
+    ms = barrier_max(_timed(lambda: sim.step(1), steps, clk=clk), ws)
+    sim.close()
+    peak, _ = measured_peaks()
+    return {"n": n, "bc": "fullway", "order": 4, "ms_per_step": ms, "mlups": n ** 4 / (ms * 1e-3) / 1e6,
+            "frac_of_interior_roofline": 528 * n ** 4 / (ms * 1e-3) / 1e9 / peak, "boundary_nodes": sim.n_boundary}
 
 
 def differentiation_workload(clk, n=128, T=1024, reps=3):
@@ -901,7 +930,8 @@ def main():
     ap.add_argument("--error-steps", type=int, default=2000)
     ap.add_argument("--oracle-steps", type=int, default=50)
     ap.add_argument("--extra-forms", type=int, default=1,
-                    help="default line: also measure the precision form and the differentiation workload at 128^3")
+                    help="default line: also measure the precision form and the differentiation workload at 128^3 "
+                         "and the D4Q33 64^4 Dirichlet box")
     ap.add_argument("--workload", default="d3q19_256",
                     choices=["d3q19_256", "d4q33_dirichlet", "d5q51_fp32dev", "adjoint", "convergence",
                              "order_law", "examples", "stability_map", "fp32_floor"])

@@ -81,8 +81,9 @@ __global__ void __launch_bounds__(128) k_boundary(const BoundaryArgs a) {
       v[k] = bnode_unknown<D, KIND, DEV>(a, nd, k, site);
     }
   }
-  // collision, as in the bulk: phi = sum_k f_k (fixed-point sum), f*_k = (1 - s) f_k + omega_k (s phi + dt R)
-  const double phi = fixed_moment_sum<Q, 0>(v);
+  // collision, as in the bulk: phi = sum_k f_k (the split moment sum of the row kernels), f*_k = (1 - s) f_k +
+  // omega_k (s phi + dt R)
+  const double phi = split_moment_sum<Q, kBoxFixedTerms<Q>>(v);
   const double psi = fma(a.s, phi, a.dt * (a.Rfield ? __ldg(a.Rfield + site) : a.R));
   const bool s2 = a.s == 2.0;
   if (DEV) {

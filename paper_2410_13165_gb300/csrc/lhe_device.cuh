@@ -151,6 +151,27 @@ __device__ __forceinline__ double fixed_moment_sum(const double (&f)[Q]) {
   return fixed_moment_sum_impl<Q, P2>([&](int k) { return f[k]; });
 }
 
+// Moment sum of the FP64 step kernels of the larger lattices. The fixed-point sum's integer work grows
+// with Q while the FP64 pipe, which the collision keeps about half busy, has room: the first NFX terms
+// are summed in fixed point and the rest added on the FP64 pipe. The split is chosen per kernel from
+// scans on GB300 (number of fixed-point terms): the periodic step splits D5Q51 only (38 of 51: 24^5
+// 1.269 -> 1.148 ms; a D4Q33 split made the 48^4 step slower, 0.444 -> 0.467 ms), the row kernels of
+// Dirichlet boxes split D4Q33 as well (29 of 33: 64^4 1.711 -> 1.672 ms). The error is within
+// (Q - NFX + 1) / 2 units in the last place of the sum (the oracle's sequential FP64 sum: up to
+// (Q - 1) / 2).
+template <int Q>
+constexpr int kPeriodicFixedTerms = Q == 51 ? 38 : Q;
+template <int Q>
+constexpr int kBoxFixedTerms = Q == 51 ? 38 : (Q == 33 ? 29 : Q);
+
+template <int Q, int NFX>
+__device__ __forceinline__ double split_moment_sum(const double (&f)[Q]) {
+  double s = fixed_moment_sum_impl<NFX, 0>([&](int k) { return f[k]; });
+#pragma unroll
+  for (int k = NFX; k < Q; ++k) s += f[k];
+  return s;
+}
+
 // Double-float storage of the macroscopic variable of the FP32-deviation form: phi = h + l with h
 // the value truncated to 24 significant bits and l the rounded residual (a 48-bit significand,
 // relative spacing 2^-48). Neighbour differences are then plain FP32 arithmetic.

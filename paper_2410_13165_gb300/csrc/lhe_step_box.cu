@@ -97,8 +97,9 @@ __global__ void __launch_bounds__(LHE_STEP_THREADS) k_step_box(const StepArgs a,
     const int j = L.e[k][0] == 1 ? xface_link<D>(k, 1) : xface_link<D>(k, -1);
     f[k] = __ldg(unknown ? rec + j : src + k * S + source_site<D, false>(L, k, site, om, op));
   }
-  const double psi = MODE == kModeS2 ? fixed_moment_sum<Q, 1>(f) + (a.Rfield ? a.dt * Rs : a.dtR)
-                                     : fma(a.sig, fixed_moment_sum<Q, 0>(f), a.Rfield ? a.rho_dt * Rs : a.rho_dtR);
+  const double sum = split_moment_sum<Q, kBoxFixedTerms<Q>>(f);  // the split moment sum of the larger lattices (lhe_device.cuh)
+  const double psi = MODE == kModeS2 ? fma(2.0, sum, a.Rfield ? a.dt * Rs : a.dtR)
+                                     : fma(a.sig, sum, a.Rfield ? a.rho_dt * Rs : a.rho_dtR);
 #pragma unroll
   for (int k = 0; k < Q; ++k) {
     const double out = MODE == kModeS2 ? fma(a.omega[k], psi, -f[k]) : fma(a.omega[k], psi, a.mu * f[k]);
@@ -281,8 +282,10 @@ __global__ void __launch_bounds__(LHE_STEP_THREADS) k_step_box_dense(const StepA
     for (int i = 0; i < D; ++i) o -= L.e[k][i] * a.g.stride[i];
     f[k] = __ldg(row_unknown ? bdata + k * S + site : (x_unknown ? xrow + jx : src + k * S + o));
   }
-  const double psi = MODE == kModeS2 ? fixed_moment_sum<Q, 1>(f) + (a.Rfield ? a.dt * Rs : a.dtR)
-                                     : fma(a.sig, fixed_moment_sum<Q, 0>(f), a.Rfield ? a.rho_dt * Rs : a.rho_dtR);
+  // the split moment sum of the larger lattices (lhe_device.cuh)
+  const double sum = split_moment_sum<Q, kBoxFixedTerms<Q>>(f);
+  const double psi = MODE == kModeS2 ? fma(2.0, sum, a.Rfield ? a.dt * Rs : a.dtR)
+                                     : fma(a.sig, sum, a.Rfield ? a.rho_dt * Rs : a.rho_dtR);
 #pragma unroll
   for (int k = 0; k < Q; ++k) {
     const double out = MODE == kModeS2 ? fma(a.omega[k], psi, -f[k]) : fma(a.omega[k], psi, a.mu * f[k]);

@@ -20,25 +20,6 @@ namespace lhe {
 // Template collision forms: s = 2, general s (mu, sig, rho from StepArgs), scaled representation.
 constexpr int kModeGeneral = 0, kModeS2 = 1, kModeScaled = 2;
 
-// Moment sum of the step kernel. For Q <= 33 the fixed-point sum (integer pipes, error below one unit
-// in the last place of the largest term). For D5Q51 the integer work of 51 fixed-point terms bounds the
-// kernel while the FP64 pipe, which the collision keeps about half busy, has room: the first 38 terms
-// are summed in fixed point and the other 13 added on the FP64 pipe (scanned 17..46; measured 1.269 ->
-// 1.148 ms per 24^5 step). The error is then within ~7 units in the last place of the sum (the oracle's
-// sequential FP64 sum: up to 25).
-template <int Q>
-__device__ __forceinline__ double step_moment_sum(const double (&f)[Q]) {
-  if constexpr (Q == 51) {
-    constexpr int NFX = 38;
-    double s = fixed_moment_sum_impl<NFX, 0>([&](int k) { return f[k]; });
-#pragma unroll
-    for (int k = NFX; k < Q; ++k) s += f[k];
-    return s;
-  } else {
-    return fixed_moment_sum<Q, 0>(f);
-  }
-}
-
 template <int D, bool ADJ, bool INTERIOR, int MODE>
 __global__ void __launch_bounds__(LHE_STEP_THREADS) k_step_fp64(const StepArgs a) {
   constexpr Lattice<D> L{};
@@ -59,8 +40,8 @@ __global__ void __launch_bounds__(LHE_STEP_THREADS) k_step_fp64(const StepArgs a
 #pragma unroll
   for (int k = 0; k < Q; ++k) f[k] = __ldg(src + k * S + source_site<D, ADJ>(L, k, site, om, op));
   double psi;
-  if (Q == 51) {  // the mixed sum (step_moment_sum); 2 w and 2 phi are exact doublings
-    const double w = step_moment_sum<Q>(f);
+  if (kPeriodicFixedTerms<Q> < Q) {  // the split sum (lhe_device.cuh); 2 w and 2 phi are exact doublings
+    const double w = split_moment_sum<Q, kPeriodicFixedTerms<Q>>(f);
     if (ADJ) {
       psi = MODE == kModeS2 ? 2.0 * w : a.sig * w;
       if (a.gR) a.gR[site] = MODE == kModeS2 ? fma(a.half_dt, psi, a.gR[site]) : fma(a.gsc, w, a.gR[site]);

@@ -45,3 +45,26 @@ def test_two_rank_timing_takes_the_slowest_rank():
     assert [g[1] for g in got] == [15.0, 15.0]
     # whole job: 2 ranks x 1000 updates in 15 ms
     assert abs(got[0][2] - 2 * 1000 / 15e-3 / 1e6) < 1e-12
+
+
+def test_clock_sampler_windows_and_reasons():
+    """The clock record of a bench line: samples inside each timed region only (by nvidia-smi's own
+    timestamps), the median SM clock, and every throttle reason seen in them."""
+    import datetime
+
+    import bench
+
+    clk = bench.ClockSampler(0, interval_ms=20)
+    t0 = datetime.datetime(2026, 1, 1, 12, 0, 0)
+    ms = lambda k: t0 + datetime.timedelta(milliseconds=k)  # noqa: E731
+    clk.samples = [(ms(0), 1500.0, 2070.0, set()), (ms(20), 2070.0, 2070.0, set()),
+                   (ms(40), 2070.0, 2070.0, {"sw_power_cap"}), (ms(60), 1800.0, 2070.0, {"hw_slowdown"}),
+                   (ms(80), 2070.0, 2070.0, set())]
+    one = clk.summary(ms(10), ms(45))
+    assert one["samples"] == 2 and one["sm_mhz"] == 2070.0 and one["reasons"] == ["sw_power_cap"]
+    assert abs(one["window_s"] - 0.035) < 1e-12
+    clk.windows = [(ms(10), ms(25)), (ms(55), ms(85))]
+    both = clk.summary_windows()
+    assert both["samples"] == 3 and both["windows"] == 2 and both["reasons"] == ["hw_slowdown"]
+    assert both["sm_mhz"] == 2070.0
+    assert clk.summary()["samples"] == 5

@@ -57,6 +57,11 @@ def workload(n):
             "e2e_job": "H2D phi0+grad (pinned), init, %d fp64 steps at tau=%g, macro, D2H phi" % (E2E_STEPS, TAU_DEV)}
 
 
+# the sources that define k_step_fp64: its translation unit and the device headers it inlines
+FP64_KERNEL_SOURCES = [os.path.join(ROOT, "paper_2410_13165_gb300", "csrc", f)
+                       for f in ("lhe_step_fp64.cu", "lhe_device.cuh", "lhe_sites.cuh", "lhe_internal.h")]
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -66,15 +71,25 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
-def profiled_traffic(kernel_src: str):
-    """DRAM bytes per launch of the FP64 step kernel from the committed ncu summary, if the kernel
-    source is unchanged since the capture (the summary records the source hash)."""
+def kernel_sources_hash(paths) -> str:
+    """First 16 hex digits of the SHA-256 of the given source files, concatenated in order."""
+    h = hashlib.sha256()
+    for p in paths:
+        with open(p, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel_srcs):
+    """DRAM bytes per launch of the FP64 step kernel from the committed ncu summary, if the kernel's
+    sources (its translation unit and the device headers it inlines) are unchanged since the capture
+    (the summary records their hash)."""
     path = os.path.join(ROOT, "profiles", "fp64_step_d3q19_256.md")
     try:
         txt = open(path).read()
     except OSError:
         return None
-    h = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()[:16]
+    h = kernel_sources_hash(kernel_srcs)
     want = None
     for line in txt.splitlines():
         if line.startswith("source_sha256_16:"):
@@ -371,8 +386,7 @@ def _run_ours(args, clk):
         # the Dirichlet box of Example 3 (D4Q33 64^4, full-way, order 4)
         forms["dirichlet_d4q33_64"] = dirichlet_box_form(clk, ws)
     fp64 = forms["fp64"]
-    kernel_src = os.path.join(ROOT, "paper_2410_13165_gb300", "csrc", "lhe_step_fp64.cu")
-    traffic = profiled_traffic(kernel_src)
+    traffic = profiled_traffic(FP64_KERNEL_SOURCES)
 
     # e2e through the public API with host buffers (FP64 path, whole job)
     e2e = None

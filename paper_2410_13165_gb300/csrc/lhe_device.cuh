@@ -196,9 +196,11 @@ __device__ __forceinline__ float2 df_add(float h, float t) {
   return make_float2(hn, __fadd_rn(__fsub_rn(s, hn), e));
 }
 
-// Streaming stores: the new state is not re-read by this kernel.
-__device__ __forceinline__ void st_stream(double *p, double v) { __stcs(p, v); }
-__device__ __forceinline__ void st_stream(float *p, float v) { __stcs(p, v); }
+// Stores of the new state with the default cache policy. The evict-first hint (st.global.cs) was
+// measured 0.6-1.7 % slower on every step kernel (D3Q19 256^3 FP64 744.6 vs 739.8 us, D4Q33 48^4 FP32
+// deviations 252.9 vs 248.6 us), bitwise the same results.
+__device__ __forceinline__ void st_stream(double *p, double v) { *p = v; }
+__device__ __forceinline__ void st_stream(float *p, float v) { *p = v; }
 
 // Programmatic dependent launch. A step kernel lets the next kernel of its stream be scheduled as
 // soon as every CTA of this one is running (pdl_trigger), and waits for the kernel before it to

@@ -22,12 +22,15 @@
 namespace lhe {
 
 // Register caps for the large lattices: D4Q33 at 5 resident blocks per SM (96 registers, no spills)
-// and D5Q51 at 4 (128 registers; 126 and no spills with its two-pass form below) keep more loads in
-// flight per SM; measured 71 -> 87 % and 66 -> 74 % of the HBM bandwidth (D4Q33 48^4, D5Q51 24^5), 76 %
-// for D5Q51 in two passes. The FP64 kernel is not capped: there the spills cost more than the occupancy
-// gains (D5Q51 76 -> 66 %).
+// and D5Q51 at 3 (168 registers, no spills). More registers per thread keep more of a node's loads in
+// flight, more resident warps hide more latency; measured on this kernel, in % of the HBM copy
+// bandwidth: D4Q33 48^4 uncapped 71 %, cap of 5 blocks 88 % (of 3 or 4: 87.6 %); D5Q51 24^5 uncapped
+// (146 registers) 66 %, 4 blocks (128 registers, spills) 74 %, 2 blocks (196 registers) 69 %, 3 blocks
+// 84 %. (A two-pass form for D5Q51, which reads the pulled values again for the new deviations so that
+// 126 registers suffice at 4 blocks, measured 77 %.) The FP64 kernel is not capped: there the spills
+// cost more than the occupancy gains (D5Q51 76 -> 66 %).
 template <int D>
-constexpr int dev_min_blocks() { return D == 4 ? 5 : (D == 5 ? 4 : 1); }
+constexpr int dev_min_blocks() { return D == 4 ? 5 : (D == 5 ? 3 : 1); }
 
 template <int D, bool ADJ, bool INTERIOR, bool S2>
 __global__ void __launch_bounds__(LHE_STEP_THREADS, dev_min_blocks<D>()) k_step_dev(const StepArgs a) {
@@ -50,47 +53,6 @@ __global__ void __launch_bounds__(LHE_STEP_THREADS, dev_min_blocks<D>()) k_step_
   const float2 p0 = __ldg(phis + site);
   const bool field = !ADJ && a.Rfield != nullptr;
   const float oms = (float)a.oms;
-  if constexpr (D == 5) {
-    // D5Q51: two passes over the links with the same operations in the same order. The first forms the
-    // moment update and keeps nothing per link; the second reads the pulled values again (mostly from
-    // L1) for the new deviations. With 51 links the one-pass form holds 102 floats per node in
-    // registers; here that pressure goes, and the loads of neighbouring lanes stay in flight
-    // (measured 0.681 -> 0.658 ms per 24^5 step).
-    float accw = 0.0f, accg = 0.0f;
-#pragma unroll
-    for (int k = 0; k < Q; ++k) {
-      const int32_t o = source_site<D, ADJ>(L, k, site, om, op);
-      const float g = __ldg(src + k * S + o);
-      float dl = 0.0f;
-      if (k != 0) {
-        const float2 pk = __ldg(phis + o);
-        dl = (pk.x - p0.x) + (pk.y - p0.y);
-      }
-      accw = fmaf(a.omega_f[k], dl, accw);
-      accg += g;
-    }
-    const float Delta = accw + accg;
-    const float2 pn = df_add(p0.x, p0.y + Delta);
-    a.phi_dst[site] = pn;
-    if (ADJ && a.gR) a.gR[site] = fma(a.dt, df_value(pn), a.gR[site]);
-    float dtR = 0.0f;
-    if (field) dtR = (float)(a.dt * __ldg(a.Rfield + site));
-#pragma unroll
-    for (int k = 0; k < Q; ++k) {
-      const int32_t o = source_site<D, ADJ>(L, k, site, om, op);
-      const float g = __ldg(src + k * S + o);
-      float dl = 0.0f;
-      if (k != 0) {
-        const float2 pk = __ldg(phis + o);
-        dl = (pk.x - p0.x) + (pk.y - p0.y);
-      }
-      const float r = fmaf(a.omega_f[k], dl - Delta, g);  // pre-collision deviation g_k
-      const float src_k = ADJ ? 0.0f : (field ? a.omega_f[k] * dtR : a.dtwR_f[k]);
-      const float out = S2 ? (src_k - r) : fmaf(oms, r, src_k);
-      st_stream(dst + k * S + site, out);
-    }
-    return;
-  }
   float dl[Q], gk[Q];
   float accw = 0.0f, accg = 0.0f;
 #pragma unroll

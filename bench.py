@@ -651,7 +651,8 @@ def run_d5q51_fp32dev(args, clk):
     for prec, bps in (("fp64", 816), ("fp32dev", 424)):
         sim = LBM(5, n, u=u, precision=prec)
         sim.init(phi0, grad)
-        ms = _timed(lambda: sim.step(1), args.steps, clk=clk)
+        # at least 200 steps (0.1-0.2 s), so that the clock sampler sees the timed region several times
+        ms = _timed(lambda: sim.step(1), max(args.steps, 200), clk=clk)
         res[prec] = {"mlups": n ** 5 / (ms * 1e-3) / 1e6, "ms_per_step": ms,
                      "gbs": bps * n ** 5 / (ms * 1e-3) / 1e9, "bytes_per_site": bps}
         sim.close()

@@ -398,12 +398,22 @@ def _run_ours(args, clk):
         d_grad = torch.empty_like(grad)
         sim = sims["fp64_tau%g" % TAU_DEV]
 
+        # events between the phases of a job (host-to-device copies, init, steps, macro, device-to-host)
+        ph = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+
         def job():
+            ph[0].record(stream)
             d_phi0.copy_(h_phi0, non_blocking=True)
             d_grad.copy_(h_grad, non_blocking=True)
+            ph[1].record(stream)
             sim.init(d_phi0, d_grad)
+            ph[2].record(stream)
             sim.step(E2E_STEPS)
-            h_out.copy_(sim.macro(), non_blocking=True)
+            ph[3].record(stream)
+            m = sim.macro()
+            ph[4].record(stream)
+            h_out.copy_(m, non_blocking=True)
+            ph[5].record(stream)
 
         job()
         barrier(ws)
@@ -414,9 +424,11 @@ def _run_ours(args, clk):
         b.record(stream)
         barrier(ws)
         e2e_ms = barrier_max(a.elapsed_time(b) / args.e2e_steps, ws)
+        names = ("h2d", "init", "steps", "macro", "d2h")
         e2e = {"value": whole_job_mlups(S * E2E_STEPS, ws, e2e_ms), "unit": UNIT, "ms_per_job": e2e_ms,
                "h2d_bytes_per_step": (h_phi0.numel() + h_grad.numel()) * 8, "d2h_bytes_per_step": h_out.numel() * 8,
-               "lb_steps_per_job": E2E_STEPS}
+               "lb_steps_per_job": E2E_STEPS,
+               "last_job_phases_ms": {nm: ph[i].elapsed_time(ph[i + 1]) for i, nm in enumerate(names)}}
 
     cpu = None
     if rank == 0 and args.cpu_baseline:

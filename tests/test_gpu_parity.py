@@ -230,6 +230,23 @@ def test_fp64_dirichlet_all_dimensions(bc, d, n, u, tau):
     assert rel(g, o) < FP64_TOL
 
 
+@pytest.mark.parametrize("precision,tol", [("fp64", FP64_TOL), ("fp32dev", DEV_TOL)])
+@pytest.mark.parametrize("bc", ["periodic", "fullway", "halfway"])
+@pytest.mark.parametrize("tau,u,R", [(1.0, (0.1, -0.05, 0.08), 0.0), (1.0, (0.1, -0.05, 0.08), 0.7),
+                                     (0.5, (0.0, 0.0, 0.0), 0.7), (1.0, (0.0, 0.0, 0.0), 0.0),
+                                     (1.7, (0.05, 0.02, -0.03), 0.3)])
+def test_degenerate_relaxation_and_velocity(precision, tol, bc, tau, u, R):
+    """The method's degenerate cases on a ragged D3Q19 box: tau = 1 (s = 1: the collision keeps
+    nothing of the pre-collision populations, f* = omega phi + dt omega R; the scaled FP64 state,
+    which stores (1 - s)^-j f*, does not apply), u = 0 (no transport: with the s = 2 collision phi
+    changes by the source alone), and tau > 1 (s < 1), each with and without a source."""
+    n = (9, 8, 7)
+    h = 1.0 / 16
+    hi = [(ni - 1) * h if bc == "fullway" else ni * h for ni in n]
+    g, o = run_pair(3, n, u, 25, hi=hi, tau=tau, R=R, bc=bc, precision=precision, nmodes=3, seed=41)
+    assert rel(g, o) < tol
+
+
 # ------------------------------------------------------------------------------ FP32 deviations
 
 def test_fp32dev_d3q19_periodic():

@@ -493,6 +493,8 @@ lhe_status lhe_lbm_create(const lhe_lbm_params *p, lhe_lbm **out) {
           }
         }
         std::sort(ent.begin(), ent.end());
+        l->nrow_ent = 0;
+        while (l->nrow_ent < (int64_t)ent.size() && ent[(size_t)l->nrow_ent].cls == 0) ++l->nrow_ent;
         std::vector<long long> ek(ent.size()), ed(ent.size()), eo(ent.size());
         std::vector<int32_t> er(ent.size());  // record (node-major) -> entry
         const int J = 2 * p->d - 1;
@@ -834,9 +836,13 @@ static BoundaryArgs boundary_args(const lhe_lbm *l) {
       bool opp = true;
       for (int i = 0; i < l->p.d; ++i)
         if (l->e[j * l->p.d + i] != -l->e[k * l->p.d + i]) opp = false;
-      if (opp) b.wratio[k] = l->omega[k] / l->omega[j];
+      if (opp) {
+        b.wratio[k] = l->omega[k] / l->omega[j];
+        b.kbar[k] = (int8_t)j;
+      }
     }
   }
+  b.nrow_ent = l->nrow_ent;
   b.s = l->s;
   b.oms = 1.0 - l->s;
   b.R = l->R;

@@ -139,6 +139,10 @@ struct BoundaryArgs {
   // P + lt_k + sum_m (A_m cos psi_m + B_m sin psi_m), psi_m = theta_m - kappa_m . u t_eval (ph_c, ph_s),
   // lt_k the part linear in t_eval (one value per link and step)
   double lt[kMaxQ];
+  // the dense boundary data (k_bdata_step): entries [0, nrow_ent) are row links, whose places in the
+  // dense array (k S + x) and half-way partners (kbar S + x) follow from the entry's (k, x)
+  int64_t nrow_ent;
+  int8_t kbar[kMaxQ];      // the link opposite to k
 };
 
 struct InitArgs {
@@ -279,6 +283,7 @@ struct lhe_lbm {
   std::vector<int32_t> bsites_host;  // boundary nodes in the library's order
   std::vector<int32_t> broff_host;   // per boundary node: first record (unknown links in the order of k)
   int64_t nrec = 0;             // records = (boundary node, unknown link) pairs
+  int64_t nrow_ent = 0;         // dense boundary data: entries of row links (the first ones)
   int32_t *broff = nullptr;     // device copies, allocated by the first lhe_lbm_set_boundary_jet
   double *brec = nullptr;
   // lhe_lbm_set_boundary_sine_product: records and source at unit time factor, scaled every step

@@ -141,7 +141,7 @@ __device__ __forceinline__ void site_coords(const Geom &g, int32_t site, int (&x
 // sin(k.x) sin psi.
 template <int D, int KIND>
 __device__ __forceinline__ void family_sep_coefs(const BoundaryArgs &b, int k, double G, const double *sn,
-                                                 const double *cs, double *p, int st) {
+                                                 const double *cs, double *p, int64_t st) {
   constexpr int Q = Lattice<D>::Q;
   const int M = b.nmodes;
   const double *coef = b.table;                        // [m][k][2]
@@ -166,7 +166,7 @@ __device__ __forceinline__ void family_sep_coefs(const BoundaryArgs &b, int k, d
 
 // The family's data from separable coefficients p (stride st) at this step: P + lt_k + sum_m (A_m cos psi_m
 // + B_m sin psi_m).
-__device__ __forceinline__ double family_sep_value(const BoundaryArgs &b, int k, const double *p, int st) {
+__device__ __forceinline__ double family_sep_value(const BoundaryArgs &b, int k, const double *p, int64_t st) {
   double v = __ldg(p) + b.lt[k];
   for (int m = 0; m < b.nmodes; ++m) {
     v = fma(__ldg(p + (1 + 2 * m) * st), b.ph_c[m], v);
@@ -204,7 +204,8 @@ __device__ __forceinline__ uint64_t row_links_out(const Geom &g, const int (&x)[
   return m;
 }
 
-// Separable coefficients of the family's data per entry, sep[e C + c], C = 1 + 2M. Once per data set.
+// Separable coefficients of the family's data per entry, sep[c nent + e] (c < 1 + 2M: each coefficient
+// contiguous over the entries, so that the per-step producer's loads are coalesced). Once per data set.
 template <int D, int KIND>
 __global__ void __launch_bounds__(128) k_family_sep(const BoundaryArgs b, const long long *__restrict__ ent,
                                                     int64_t nent, double *__restrict__ sep) {
@@ -225,15 +226,17 @@ __global__ void __launch_bounds__(128) k_family_sep(const BoundaryArgs b, const 
     for (int i = 0; i < D; ++i) ph = fma(b.kappa[m * kMaxD + i], b.x0[i] + (double)x[i] * b.dx, ph);
     sincos(ph, &sn[m], &cs[m]);
   }
-  family_sep_coefs<D, KIND>(b, k, G, sn, cs, sep + e * (1 + 2 * b.nmodes), 1);
+  family_sep_coefs<D, KIND>(b, k, G, sn, cs, sep + e, nent);
 }
 
 // The unknown populations of this step into the dense array, one thread per entry (k, x): the records
 // (formed in the order of the entries) times rec_scale, or the family's data from its separable
 // coefficients (lt, ph_c, ph_s of the step in b); half-way minus f*_kbar(x) of the state at the start
-// of the step (a.src). The same operations, in the same order, as the boundary-node kernel.
-// dst[e] is the entry's place in the dense array (k S + x) or, for the row-end entries, after it
-// (Q S + (2 row + h) J + jx); opp[e] = kbar S + x, the population subtracted by the half-way scheme.
+// of the step (b.src). The same operations, in the same order, as the boundary-node kernel.
+// A row entry (e < nrow_ent) goes to k S + x of the dense array and its half-way partner is kbar S + x,
+// both formed from the entry's (k, x) (two 8-byte index loads fewer per entry); dst[e] is the entry's
+// place in the dense array (k S + x) or, for the row-end entries, after it (Q S + (2 row + h) J + jx),
+// and opp[e] = kbar S + x.
 template <int KIND, bool REC>
 __global__ void __launch_bounds__(256) k_bdata_step(const BoundaryArgs b, const long long *__restrict__ ent,
                                                     const long long *__restrict__ dst, const long long *__restrict__ opp,
@@ -241,10 +244,15 @@ __global__ void __launch_bounds__(256) k_bdata_step(const BoundaryArgs b, const 
                                                     double *__restrict__ bdata) {
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= nent) return;
-  double v = REC ? b.rec_scale * __ldg(data + e)
-                 : family_sep_value(b, (int)(__ldg(ent + e) >> 32), data + e * (1 + 2 * b.nmodes), 1);
-  if (KIND == 2) v = v - __ldg(static_cast<const double *>(b.src) + __ldg(opp + e));
-  bdata[__ldg(dst + e)] = v;
+  // (full-way records need no (k, x): their dst[e] costs the same bytes as the entry)
+  const bool row = (!REC || KIND == 2) && e < b.nrow_ent;
+  const long long tg = (row || !REC) ? __ldg(ent + e) : 0ll;
+  const int k = (int)(tg >> 32);
+  const long long x = tg & 0xffffffffll;
+  double v = REC ? b.rec_scale * __ldg(data + e) : family_sep_value(b, k, data + e, nent);
+  if (KIND == 2)
+    v = v - __ldg(static_cast<const double *>(b.src) + (row ? (long long)b.kbar[k] * b.g.S + x : __ldg(opp + e)));
+  bdata[row ? (long long)k * b.g.S + x : __ldg(dst + e)] = v;
 }
 
 // FP64 step of every node of a Dirichlet box (whole rows, x_1 fastest): each population is the pulled

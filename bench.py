@@ -80,11 +80,11 @@ def kernel_sources_hash(paths) -> str:
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(kernel_srcs):
+def profiled_traffic(kernel_srcs, path=None):
     """DRAM bytes per launch of the FP64 step kernel from the committed ncu summary, if the kernel's
     sources (its translation unit and the device headers it inlines) are unchanged since the capture
     (the summary records their hash)."""
-    path = os.path.join(ROOT, "profiles", "fp64_step_d3q19_256.md")
+    path = path or os.path.join(ROOT, "profiles", "fp64_step_d3q19_256.md")
     try:
         txt = open(path).read()
     except OSError:

@@ -68,3 +68,29 @@ def test_clock_sampler_windows_and_reasons():
     assert both["samples"] == 3 and both["windows"] == 2 and both["reasons"] == ["hw_slowdown"]
     assert both["sm_mhz"] == 2070.0
     assert clk.summary()["samples"] == 5
+
+
+def test_profiled_traffic_needs_the_sources_the_counters_were_taken_on(tmp_path):
+    """The roofline's `traffic` comes from the committed ncu summary only while the kernel's sources
+    hash to the value recorded beside the counters; a changed source, a missing or malformed summary
+    give null."""
+    import sys
+
+    sys.path.insert(0, ROOT)
+    import bench
+
+    srcs = []
+    for i, text in enumerate(("kernel a\n", "header b\n")):
+        f = tmp_path / ("src%d.cu" % i)
+        f.write_text(text)
+        srcs.append(str(f))
+    h = bench.kernel_sources_hash(srcs)
+    assert len(h) == 16 and h != bench.kernel_sources_hash(srcs[::-1])
+    prof = tmp_path / "prof.md"
+    prof.write_text("# k\n\nsource_sha256_16: %s\ndram_bytes_per_launch: 5042171904\n" % h)
+    assert bench.profiled_traffic(srcs, str(prof)) == 5042171904.0
+    (tmp_path / "src1.cu").write_text("header b, changed\n")
+    assert bench.profiled_traffic(srcs, str(prof)) is None
+    assert bench.profiled_traffic(srcs, str(tmp_path / "missing.md")) is None
+    prof.write_text("no counters here\n")
+    assert bench.profiled_traffic(srcs, str(prof)) is None

@@ -81,7 +81,11 @@ typedef enum { LHE_M4_RULE = 0, LHE_M4_EXPLICIT = 1 } lhe_m4_mode;
  * later step kernels of one lhe_lbm_step / lhe_lbm_adjoint_step call are launched with programmatic
  * stream serialization: such a kernel may be scheduled while the step before it finishes, and waits
  * for that step to complete before it touches global memory (same results, shorter gaps between
- * consecutive steps). The first kernel of a call is always ordered plainly behind the stream. */
+ * consecutive steps). So is the first step kernel of a call when the step kernels that the library
+ * launched last, in this process, were this handle's and on the same stream (consecutive calls of one
+ * handle); work that the caller queued in between keeps its ordering (such a kernel then starts only
+ * once that work is complete). Otherwise the first kernel of a call is ordered plainly behind the
+ * stream. */
 #define LHE_FLAG_NO_PDL 2
 /* LHE_FLAG_TEST_EXPIRE_WAIT: a test hook for the failure path of the staged FP32-deviation kernel. Its
  * waits for copies are bounded (1 s); on expiry the kernel stops, waits (bounded) for the copies it

@@ -3,6 +3,7 @@
 #include <cstdio>
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -304,9 +305,34 @@ DevTmaPlan staged_plan(lhe_lbm *l) {
   return p;
 }
 
-// Programmatic dependent launch between the consecutive step kernels of one step / adjoint_step call
-// (the first launch of a call keeps plain stream ordering behind whatever the caller queued).
+// Programmatic dependent launch between the consecutive step kernels of one step / adjoint_step call,
+// and for the first step kernel of a call when the step kernels the library launched last (process-wide)
+// were this handle's, on the same stream. The step kernels let their successor be scheduled as soon
+// as all their CTAs run; a successor of another handle (another grid shape, another kernel) scheduled
+// that early measured slower, so across calls only a handle's own step kernels chain this way. Work
+// that the caller queued in between does not let the successor in early (it does not signal), and a
+// successor always waits for its predecessor to complete, so the results are the same in every case.
 bool pdl_ok(const lhe_lbm *l) { return !(l->p.flags & LHE_FLAG_NO_PDL); }
+
+std::mutex g_last_steps_mu;
+const lhe_lbm *g_last_steps_handle = nullptr;  // whose step kernels the library launched last
+cudaStream_t g_last_steps_stream = nullptr;
+
+bool continues_own_steps(const lhe_lbm *l) {
+  std::lock_guard<std::mutex> lock(g_last_steps_mu);
+  return g_last_steps_handle == l && g_last_steps_stream == l->stream;
+}
+
+void note_own_steps(const lhe_lbm *l) {
+  std::lock_guard<std::mutex> lock(g_last_steps_mu);
+  g_last_steps_handle = l;
+  g_last_steps_stream = l->stream;
+}
+
+void forget_steps_of(const lhe_lbm *l) {
+  std::lock_guard<std::mutex> lock(g_last_steps_mu);
+  if (g_last_steps_handle == l) g_last_steps_handle = nullptr;
+}
 
 // The link k-bar with e_kbar = -e_k.
 int opposite_link(const lhe_lbm *l, int k) {
@@ -570,6 +596,7 @@ lhe_status lhe_lbm_create(const lhe_lbm_params *p, lhe_lbm **out) {
 
 lhe_status lhe_lbm_destroy(lhe_lbm *l) {
   if (!l) return LHE_OK;
+  forget_steps_of(l);
   cudaStreamSynchronize(l->stream);
   for (int b = 0; b < 2; ++b) {
     cudaFree(l->pop[b]);
@@ -1074,6 +1101,8 @@ lhe_status lhe_lbm_step(lhe_lbm *l, int64_t n) {
   BoundaryArgs b{};
   if (!periodic) b = boundary_args(l);
   const bool scaled = scaled_eligible(l);
+  const bool chained = n > 0 && pdl_ok(l) && continues_own_steps(l);
+  if (n > 0) note_own_steps(l);
   for (int64_t it = 0; it < n; ++it) {
     if (scaled) plan_scaled_step(l, 0, a);
     a.src = l->pop[l->cur];
@@ -1081,7 +1110,7 @@ lhe_status lhe_lbm_step(lhe_lbm *l, int64_t n) {
     a.phi_src = l->phi[l->cur];
     a.phi_dst = l->phi[1 - l->cur];
     a.nwork = periodic ? l->g.S : l->g.S_rows;
-    a.pdl = it > 0 && pdl_ok(l);
+    a.pdl = (it > 0 || chained) && pdl_ok(l);
     if (!periodic) {
       b.src = a.src;
       b.dst = a.dst;
@@ -1275,13 +1304,15 @@ lhe_status lhe_lbm_adjoint_step(lhe_lbm *l, int64_t n) {
   BoundaryArgs b{};
   if (!periodic) b = boundary_args(l);
   const bool scaled = scaled_eligible(l);
+  const bool chained = n > 0 && pdl_ok(l) && continues_own_steps(l);
+  if (n > 0) note_own_steps(l);
   for (int64_t it = 0; it < n; ++it) {
     if (scaled) plan_scaled_step(l, 1, a);
     a.src = l->adj[l->acur];
     a.dst = l->adj[1 - l->acur];
     a.phi_src = l->adjW[l->acur];
     a.phi_dst = l->adjW[1 - l->acur];
-    a.pdl = it > 0 && pdl_ok(l);
+    a.pdl = (it > 0 || chained) && pdl_ok(l);
     cudaError_t e = l->staged ? launch_step_dev3_tma(true, a, staged_plan(l), l->stream)
                     : dev         ? launch_step_dev(l->p.d, true, !periodic, a, l->stream)
                                   : launch_step_fp64(l->p.d, true, !periodic, a, l->stream);

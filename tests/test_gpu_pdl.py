@@ -82,3 +82,46 @@ def test_pdl_is_bitwise_plain_ordering(d, n, u, tau, precision, bc):
     b = _run(d, n, u, tau, precision, bc, False)
     for x, y in zip(a, b):
         assert torch.equal(x, y)
+
+
+@pytest.mark.parametrize("precision,staged", [("fp64", False), ("fp32dev", True), ("fp32dev", False)])
+def test_calls_of_one_step_chain_across_calls(precision, staged):
+    """Consecutive calls of one handle chain their step kernels with programmatic dependent launch
+    (the first kernel of a call too, when the library's last step kernels on the stream were this
+    handle's). Calls of one step, interleaved with another handle's steps on the same stream, with
+    macro and diagnostics reads and with an adjoint pass, must give the bits of the same calls with
+    plain stream ordering."""
+    import torch
+
+    n = (32, 12, 10)
+    X = W.node_coords(3, list(n), 0.0, 1.0 / 32)
+    F = W.fourier_field(3, 3, 9, 0.0, [ni / 32.0 for ni in n])
+    phi0, grad = _t(F.value(X)), _t(F.grad(X))
+
+    def run(pdl):
+        kw = dict(u=(0.1, -0.05, 0.08), tau=0.8, precision=precision, staged=staged, pdl=pdl)
+        a = LBM(3, list(n), 0.0, [ni / 32.0 for ni in n], **kw)
+        b = LBM(3, list(n), 0.0, [ni / 32.0 for ni in n], **kw)
+        for s in (a, b):
+            s.init(phi0, grad)
+        reads = []
+        for i in range(12):
+            a.step(1)
+            if i % 3 == 0:
+                b.step(1)
+            if i % 4 == 1:
+                reads.append(a.macro().clone())
+            if i == 7:
+                reads.append(torch.tensor(a.diagnostics()["mass"]))
+        a.adjoint_seed(a.macro().contiguous())
+        for _ in range(5):
+            a.adjoint_step(1)
+        gphi, _, _ = a.adjoint_grads(want_grad=False, want_R=False)
+        out = [a.get_state().clone(), b.get_state().clone(), gphi.clone()] + reads
+        a.close()
+        b.close()
+        torch.cuda.synchronize()
+        return out
+
+    for x, y in zip(run(True), run(False)):
+        assert torch.equal(x, y)

@@ -11,7 +11,9 @@ whole job over N GPUs) over the three tau; every form is reported under "forms",
 s = 2 collision) as an extra line. Inputs are resident in HBM and each population buffer (2.5 GB)
 exceeds the 126 MB L2, so no L2 flush is needed between iterations. `e2e` times the FP64 metric
 through the public API with host buffers: upload of phi0 and grad phi0 from pinned memory, init,
-1000 steps at tau = 0.8 (the workload's run length), macro and download of phi, per e2e step.
+1000 steps at tau = 0.8 (the workload's run length), macro and download of phi, per job, over
+--e2e-steps consecutive jobs whose copies run on a second stream alongside the neighbouring jobs'
+steps (the first upload and the last download of the timed region overlap nothing).
 
 Under torchrun (N > 1) every rank runs the workload on its own GPU (independent replicas: the path
 has no data exchange between boxes of one replica), timing is bracketed by a barrier and CUDA

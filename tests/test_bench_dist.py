@@ -94,3 +94,24 @@ def test_profiled_traffic_needs_the_sources_the_counters_were_taken_on(tmp_path)
     assert bench.profiled_traffic(srcs, str(tmp_path / "missing.md")) is None
     prof.write_text("no counters here\n")
     assert bench.profiled_traffic(srcs, str(prof)) is None
+
+
+def test_reference_arm_prints_its_line_on_the_host():
+    """`bench.py --impl reference` times the CPU oracle on the host cores (a tiny sample here) and
+    prints one JSON line with the contract's keys: impl, the metric of the GPU arm, a cpu_baseline
+    describing the run, and an e2e entry without copies."""
+    import json
+    import subprocess
+    import sys
+
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "2",
+                          "--warmup", "1", "--ref-n", "8"], capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert out.returncode == 0, out.stderr[-2000:]
+    line = json.loads([ln for ln in out.stdout.splitlines() if ln.startswith("{")][-1])
+    import bench
+
+    assert line["impl"] == "reference" and line["metric"] == bench.METRIC and line["unit"] == "MLUPS"
+    assert line["steps"] == 2 and line["warmup"] >= 1 and line["higher_is_better"] is True
+    assert line["value"] > 0 and line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
+    assert line["cpu_baseline"]["value"] == line["value"]
+    assert line["e2e"] == {"value": line["value"], "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
